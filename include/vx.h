@@ -1,0 +1,258 @@
+/*
+ * vx.h -- C ABI of libvx: hybrid voxel formats (Arbore et al., "Hybrid Voxel
+ * Formats for Efficient Ray Tracing") built on the host and traced on an
+ * NVIDIA B300 (sm_103a).
+ *
+ * A hybrid format is a list of levels, each one of the paper's base formats
+ * (Sec. 3.1, Table 1): Raw R(W,H,D), SVO S(L) or SVDAG G(L).  A voxel holds a
+ * 32-bit RGBA word (R | G << 8 | B << 16 | A << 24) and is empty iff all 32
+ * bits are 0 (Sec. 3).  The library builds a volume in the paper's word-buffer
+ * layout (Sec. 3.3, Fig. 3) with the Morton-order construction of Sec. 4.1 and
+ * Sec. 5, copies it to the GPU, and answers first-hit ray queries with CUDA
+ * kernels whose per-level steppers are composed at compile time (Sec. 4.2).
+ *
+ * Conventions shared by every call:
+ *   - return value 0 (VX_OK) or a negative VX_E* code; on error,
+ *     vx_last_error() returns a message for the calling thread;
+ *   - device pointers are plain CUDA device addresses owned by the caller;
+ *     host pointers are plain host addresses owned by the caller; a call never
+ *     frees memory it did not allocate;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); calls
+ *     that take one enqueue work on it and return without synchronising,
+ *     except the *_host variants, which return when their results are in host
+ *     memory;
+ *   - all calls are thread-safe for distinct volumes; a volume may be traced
+ *     from several threads/streams at once, but must not be freed while in use.
+ */
+#ifndef VX_H_
+#define VX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------- */
+/* Error codes                                                              */
+/* ----------------------------------------------------------------------- */
+#define VX_OK 0
+#define VX_EINVAL (-1)       /* bad argument, bad format spec, misaligned pointer */
+#define VX_ENOMEM (-2)       /* host or device allocation failed */
+#define VX_ECUDA (-3)        /* a CUDA call failed (message names it) */
+#define VX_ETOOBIG (-4)      /* buffer would exceed 2^32 words (Sec. 3.3) */
+#define VX_ETIMEOUT (-5)     /* a bounded device wait ran out */
+#define VX_EUNSUPPORTED (-6) /* valid request this build cannot serve */
+
+/* ----------------------------------------------------------------------- */
+/* Rays and hits                                                            */
+/* ----------------------------------------------------------------------- */
+/* One ray, 32 bytes, 16-byte aligned in arrays: points o + t d for
+ * t in [tmin, tmax], in voxel units over the box [0,nx) x [0,ny) x [0,nz).
+ * d need not be normalised.  A ray with a NaN component or an infinite tmin
+ * is reported with status VX_STATUS_INVALID. */
+typedef struct vx_ray {
+    float ox, oy, oz, tmin;
+    float dx, dy, dz, tmax;
+} vx_ray;
+
+/* Full hit record, 16 bytes (hit_layout = VX_HIT_FULL).
+ *   t      entry parameter of the hit voxel (tmin / box entry for the first
+ *          voxel); +inf on a miss;
+ *   rgba   the voxel's word; 0 on a miss;
+ *   x,y,z  voxel coordinate; 0xFFFF on a miss;
+ *   face   0 = ray starts inside the voxel, else 1 + 2*axis + (d_axis < 0):
+ *          the side the ray entered through;
+ *   status VX_STATUS_*. */
+typedef struct vx_hit {
+    float t;
+    uint32_t rgba;
+    uint16_t x, y, z;
+    uint8_t face;
+    uint8_t status;
+} vx_hit;
+
+/* Compact hit record, 8 bytes (hit_layout = VX_HIT_COMPACT): idx =
+ * x + nx*(y + ny*z), or 0xFFFFFFFF for a miss or an invalid ray; t as above.
+ * Needs nx*ny*nz < 2^32. */
+typedef struct vx_hit_compact {
+    uint32_t idx;
+    float t;
+} vx_hit_compact;
+
+#define VX_HIT_FULL 0
+#define VX_HIT_COMPACT 1
+
+#define VX_STATUS_MISS 0
+#define VX_STATUS_HIT 1
+#define VX_STATUS_INVALID 2
+#define VX_STATUS_ERROR 3 /* iteration cap or bounds check tripped */
+
+/* ----------------------------------------------------------------------- */
+/* Volumes                                                                  */
+/* ----------------------------------------------------------------------- */
+typedef struct vx_volume_s* vx_volume;
+
+/* Source grid of a build, the role of the paper's voxelizer (Sec. 4.1,
+ * Sec. 5).  Exactly one of `dense` and `fill_brick` is set.
+ *   log2_dim  grid size per axis, 2^log2_dim[i] voxels (<= 2^15);
+ *   dense     host array of 2^(sum log2_dim) RGBA words, x fastest;
+ *   fill_brick  called with a cube of side 2^log2_size whose corner
+ *             (x0,y0,z0) is a multiple of its side; writes the cube's words,
+ *             x fastest, to `out`; returns 0 on success;
+ *   block_empty optional: returns 1 only if the cube holds no occupied voxel
+ *             (lets the builder skip empty space without fetching it);
+ *   user      passed back to the callbacks. */
+typedef int (*vx_fill_brick_fn)(void* user, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t log2_size,
+                                uint32_t* out);
+typedef int (*vx_block_empty_fn)(void* user, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t log2_size);
+typedef struct vx_grid {
+    uint32_t log2_dim[3];
+    const uint32_t* dense;
+    vx_fill_brick_fn fill_brick;
+    vx_block_empty_fn block_empty;
+    void* user;
+} vx_grid;
+
+#define VX_DEDUP_PER_SUBVOLUME 0
+#define VX_DEDUP_WHOLE_LEVEL 1 /* the paper's evaluated setting (Sec. 6.1) */
+
+/* Build options (NULL = defaults).
+ *   dedup_scope   VX_DEDUP_WHOLE_LEVEL (default) or VX_DEDUP_PER_SUBVOLUME:
+ *                 one SVDAG de-duplication map per level, or one per
+ *                 sub-volume (Sec. 4.3);
+ *   device        CUDA device for the device image; -1 = current (default);
+ *   no_upload     1 = build on the host only (vx_trace then fails);
+ *   threads       host threads for the build, 0 = all cores. */
+typedef struct vx_build_opts {
+    int32_t dedup_scope;
+    int32_t device;
+    int32_t no_upload;
+    int32_t threads;
+} vx_build_opts;
+
+/* Builds `spec` over `grid` and uploads it.  Paper: Sec. 4.1 (per-level
+ * construction, Fig. 4 construct), Sec. 5 (Morton order), Sec. 3.3 (layout).
+ *   spec  format signature in Table 1's grammar with log2 extents, levels
+ *         separated by spaces: "R(4,4,4) S(2) G(3)"; "R(4^3)" abbreviates
+ *         R(4,4,4).  Each level but the first must be cubic (Sec. 5); the
+ *         extents per axis must sum to grid->log2_dim.
+ *   out   receives the handle; free it with vx_free.
+ * Errors: VX_EINVAL (spec or grid), VX_ETOOBIG (over 2^32 words, Sec. 3.3),
+ * VX_ENOMEM, VX_ECUDA, VX_EUNSUPPORTED (a level kind this build lacks). */
+int vx_build(const char* spec, const vx_grid* grid, const vx_build_opts* opts, vx_volume* out);
+
+/* Releases the host and device memory of a volume (synchronises its device
+ * first).  NULL is accepted. */
+int vx_free(vx_volume v);
+
+/* Size and build statistics of a volume.  Level k counts the words written
+ * for its structures (Raw arrays, octree node lists, DAG nodes) and its
+ * nodes: Raw sub-volumes, or octree / DAG nodes including leaf nodes. */
+#define VX_MAX_LEVELS 16
+typedef struct vx_stats {
+    uint32_t n_levels;
+    uint32_t n_node_levels;  /* levels after expanding S(L)/G(L) into L octree levels */
+    uint32_t log2_dim[3];
+    int32_t specialized;     /* 1 = a compile-time-composed kernel serves this spec */
+    uint64_t canonical_words;   /* paper-layout buffer size in words */
+    uint64_t device_bytes;      /* device image size */
+    uint64_t occupied_voxels;
+    uint64_t level_words[VX_MAX_LEVELS];
+    uint64_t level_nodes[VX_MAX_LEVELS];
+    double build_ms;
+    double upload_ms;
+} vx_stats;
+
+int vx_stats_get(vx_volume v, vx_stats* out);
+
+/* Host view of the canonical (paper-layout) word buffer: word 0 is the root
+ * pointer (Sec. 4.1).  The pointer stays valid until vx_free. */
+int vx_canonical(vx_volume v, const uint32_t** words, uint64_t* n_words);
+
+/* Decodes the voxels of an axis-aligned cube of side 2^log2_size at
+ * (x0,y0,z0) (a multiple of the side) from the canonical buffer into `out`
+ * (host, x fastest).  Host only; for checks and tools. */
+int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t log2_size, uint32_t* out);
+
+/* ----------------------------------------------------------------------- */
+/* Tracing                                                                  */
+/* ----------------------------------------------------------------------- */
+#define VX_MODE_AUTO 0       /* pick per format (autotuned when tuned) */
+#define VX_MODE_PLAIN 1      /* one thread per ray */
+#define VX_MODE_PERSISTENT 2 /* persistent warps refilled from a global ray queue */
+
+/* Trace options (NULL = defaults / autotuned values).
+ *   mode   VX_MODE_*;
+ *   block  threads per block (multiple of 32, <= 1024), 0 = default;
+ *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = default;
+ *   smem_top  1 = stage the top Raw level in shared memory when it fits,
+ *          0 = read it from global memory, -1 = default. */
+typedef struct vx_trace_opts {
+    int32_t mode;
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t smem_top;
+    int32_t reserved[4];
+} vx_trace_opts;
+
+/* First hit of each ray (Sec. 4.2: the root function reads the root pointer,
+ * tests the root box and calls the level functions, which visit non-empty
+ * sub-volumes in hit-time order, Fig. 4 intersect).
+ *   rays  device array of n vx_ray (16-byte aligned);
+ *   hits  device array of n vx_hit or vx_hit_compact (per hit_layout),
+ *         16- or 8-byte aligned;
+ * Results equal a plain FP64 Amanatides-Woo walk over the uncompressed grid.
+ * Errors: VX_EINVAL (NULL or misaligned pointers, bad layout, compact layout
+ * on a grid of 2^32 voxels or more), VX_ECUDA (launch failure). */
+int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
+             const vx_trace_opts* opts, void* stream);
+
+/* Same as vx_trace with host arrays: the rays are copied to the device in
+ * chunks, traced and the hits copied back, copies overlapped with tracing.
+ * Returns when all hits are in host memory.  Pinned host memory is fastest. */
+int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,
+                  const vx_trace_opts* opts, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Ray generation                                                           */
+/* ----------------------------------------------------------------------- */
+/* Pinhole camera: pixel (px, py), py = 0 at the top row, gets the ray through
+ * its centre: d = normalize(f + sx r + sy u) with f = normalize(look - eye),
+ * r = normalize(f x up), u = r x f, sx = (2 (px + 0.5)/W - 1) tan(vfov/2) W/H,
+ * sy = (1 - 2 (py + 0.5)/H) tan(vfov/2); origin eye, tmin 0, tmax +inf.
+ * Ray index px + W py.  (The paper renders camera views, Fig. 6; it fixes no
+ * camera model.) */
+typedef struct vx_camera {
+    double eye[3], look[3], up[3];
+    double vfov_deg;
+    uint32_t width, height;
+} vx_camera;
+
+/* Writes width*height rays to `rays` (device, 16-byte aligned). */
+int vx_raygen_pinhole(const vx_camera* cam, vx_ray* rays, void* stream);
+
+/* Pinhole rays generated and traced in one kernel (no ray array in memory);
+ * hits as for vx_trace, one per pixel. */
+int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t hit_layout, const vx_trace_opts* opts,
+              void* stream);
+
+/* Same as vx_render with the hits copied to host memory; returns when they
+ * are there. */
+int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host, int32_t hit_layout,
+                   const vx_trace_opts* opts, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Misc                                                                     */
+/* ----------------------------------------------------------------------- */
+/* Message of the last failed call on this thread ("" if none). */
+const char* vx_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int vx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VX_H_ */

@@ -1,0 +1,294 @@
+"""Hybrid voxel formats (Arbore et al., arXiv 2410.14128) traced on B300.
+
+Thin ctypes binding over ``libvx.so`` (C ABI in ``include/vx.h``).  Every step
+of tracing runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch is used for device memory and streams.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvx.so")
+
+VX_OK, VX_EINVAL, VX_ENOMEM, VX_ECUDA, VX_ETOOBIG, VX_ETIMEOUT, VX_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+HIT_FULL, HIT_COMPACT = 0, 1
+MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT = 0, 1, 2
+STATUS_MISS, STATUS_HIT, STATUS_INVALID, STATUS_ERROR = 0, 1, 2, 3
+DEDUP_PER_SUBVOLUME, DEDUP_WHOLE_LEVEL = 0, 1
+MAX_LEVELS = 16
+
+HIT_DTYPE = np.dtype([("t", "<f4"), ("rgba", "<u4"), ("x", "<u2"), ("y", "<u2"), ("z", "<u2"),
+                      ("face", "u1"), ("status", "u1")])
+COMPACT_DTYPE = np.dtype([("idx", "<u4"), ("t", "<f4")])
+assert HIT_DTYPE.itemsize == 16 and COMPACT_DTYPE.itemsize == 8
+
+
+class VxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vx error {code}: {msg}")
+        self.code = code
+
+
+FILL_BRICK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                              ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32))
+BLOCK_EMPTY = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                               ctypes.c_uint32)
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("log2_dim", ctypes.c_uint32 * 3), ("dense", ctypes.c_void_p), ("fill_brick", FILL_BRICK),
+                ("block_empty", BLOCK_EMPTY), ("user", ctypes.c_void_p)]
+
+
+class _BuildOpts(ctypes.Structure):
+    _fields_ = [("dedup_scope", ctypes.c_int32), ("device", ctypes.c_int32), ("no_upload", ctypes.c_int32),
+                ("threads", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_uint32), ("n_node_levels", ctypes.c_uint32), ("log2_dim", ctypes.c_uint32 * 3),
+                ("specialized", ctypes.c_int32), ("canonical_words", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("occupied_voxels", ctypes.c_uint64),
+                ("level_words", ctypes.c_uint64 * MAX_LEVELS), ("level_nodes", ctypes.c_uint64 * MAX_LEVELS),
+                ("build_ms", ctypes.c_double), ("upload_ms", ctypes.c_double)]
+
+
+class _TraceOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("smem_top", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class _Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_double * 3), ("look", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("vfov_deg", ctypes.c_double), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
+
+
+_lib = None
+
+# Every entry point of include/vx.h, with its ctypes signature.
+_SIGS = {
+    "vx_build": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_Grid), ctypes.POINTER(_BuildOpts),
+                                ctypes.POINTER(ctypes.c_void_p)]),
+    "vx_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "vx_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Stats)]),
+    "vx_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint64)]),
+    "vx_decode_brick": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_void_p]),
+    "vx_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32,
+                                ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_raygen_pinhole": (ctypes.c_int, [ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_void_p]),
+    "vx_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_render_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_last_error": (ctypes.c_char_p, []),
+    "vx_version": (ctypes.c_int, []),
+}
+
+
+def lib():
+    """Loads libvx.so (building it first if it is absent)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import _build
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != VX_OK:
+        raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
+
+
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, smem_top=-1):
+    o = _TraceOpts()
+    o.mode, o.block, o.blocks_per_sm, o.smem_top = mode, block, blocks_per_sm, smem_top
+    return o
+
+
+def _camera(cam: dict) -> _Camera:
+    c = _Camera()
+    for i in range(3):
+        c.eye[i], c.look[i], c.up[i] = cam["eye"][i], cam["look"][i], cam["up"][i]
+    c.vfov_deg = float(cam["vfov_deg"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def hit_dtype(layout: int):
+    return HIT_DTYPE if layout == HIT_FULL else COMPACT_DTYPE
+
+
+def alloc_hits(n: int, layout: int = HIT_FULL, device="cuda"):
+    """Device tensor for n hit records (int32 words)."""
+    import torch
+    words = 4 if layout == HIT_FULL else 2
+    return torch.empty((n, words), dtype=torch.int32, device=device)
+
+
+def hits_to_numpy(hits, layout: int = HIT_FULL) -> np.ndarray:
+    """Structured numpy view of a hit tensor (copied to the host)."""
+    a = hits.detach().cpu().numpy() if hasattr(hits, "detach") else np.asarray(hits)
+    return np.ascontiguousarray(a).view(hit_dtype(layout)).reshape(-1)
+
+
+class Volume:
+    """A hybrid-format volume: built on the host, resident on one GPU."""
+
+    def __init__(self, spec: str, grid: np.ndarray | None = None, *, log2_dim=None, fill_brick=None,
+                 block_empty=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1, upload: bool = True):
+        L = lib()
+        g = _Grid()
+        self._keep = []
+        if grid is not None:
+            arr = np.ascontiguousarray(grid, dtype=np.uint32)
+            nz, ny, nx = arr.shape
+            dims = []
+            for n in (nx, ny, nz):
+                if n & (n - 1):
+                    raise ValueError("grid sides must be powers of two")
+                dims.append(n.bit_length() - 1)
+            self._keep.append(arr)
+            g.dense = arr.ctypes.data
+        else:
+            if fill_brick is None or log2_dim is None:
+                raise ValueError("pass a dense grid, or log2_dim and fill_brick")
+            dims = list(log2_dim)
+            cb = FILL_BRICK(fill_brick)
+            self._keep.append(cb)
+            g.fill_brick = cb
+            if block_empty is not None:
+                be = BLOCK_EMPTY(block_empty)
+                self._keep.append(be)
+                g.block_empty = be
+        for i in range(3):
+            g.log2_dim[i] = dims[i]
+        o = _BuildOpts(dedup, device, 0 if upload else 1, 0)
+        h = ctypes.c_void_p()
+        _check(L.vx_build(spec.encode(), ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.spec = spec
+        self.log2_dim = tuple(dims)
+        self._keep = []
+
+    # -- lifetime ---------------------------------------------------------
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().vx_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- host-side views --------------------------------------------------
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib().vx_stats_get(self._h, ctypes.byref(s)))
+        n = s.n_levels
+        return {
+            "n_levels": n, "n_node_levels": s.n_node_levels, "log2_dim": tuple(s.log2_dim),
+            "specialized": bool(s.specialized), "canonical_words": s.canonical_words,
+            "canonical_bytes": 4 * s.canonical_words, "device_bytes": s.device_bytes,
+            "occupied_voxels": s.occupied_voxels, "level_words": list(s.level_words)[:n],
+            "level_nodes": list(s.level_nodes)[:n], "build_ms": s.build_ms, "upload_ms": s.upload_ms,
+        }
+
+    def canonical(self) -> np.ndarray:
+        p, n = ctypes.c_void_p(), ctypes.c_uint64()
+        _check(lib().vx_canonical(self._h, ctypes.byref(p), ctypes.byref(n)))
+        return np.ctypeslib.as_array(ctypes.cast(p, ctypes.POINTER(ctypes.c_uint32)), shape=(n.value,)).copy()
+
+    def decode_brick(self, x0: int, y0: int, z0: int, log2_size: int) -> np.ndarray:
+        side = 1 << log2_size
+        out = np.zeros((side, side, side), dtype=np.uint32)
+        _check(lib().vx_decode_brick(self._h, x0, y0, z0, log2_size, out.ctypes.data))
+        return out
+
+    # -- tracing ----------------------------------------------------------
+    def trace(self, rays, hits, layout: int = HIT_FULL, stream=None, **opts):
+        """rays: CUDA tensor (n, 8) float32; hits: CUDA tensor from alloc_hits."""
+        n = rays.shape[0]
+        o = _opts(**opts)
+        _check(lib().vx_trace(self._h, ctypes.c_void_p(rays.data_ptr()), n, ctypes.c_void_p(hits.data_ptr()),
+                              layout, ctypes.byref(o), _stream_handle(stream)))
+        return hits
+
+    def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,
+                   **opts) -> np.ndarray:
+        r = np.ascontiguousarray(rays, dtype=np.float32)
+        n = r.shape[0]
+        if out is None:
+            out = np.empty(n, dtype=hit_dtype(layout))
+        o = _opts(**opts)
+        _check(lib().vx_trace_host(self._h, ctypes.c_void_p(r.ctypes.data), n, ctypes.c_void_p(out.ctypes.data),
+                                   layout, ctypes.byref(o), _stream_handle(stream)))
+        return out
+
+    def render(self, cam: dict, hits, layout: int = HIT_FULL, stream=None, **opts):
+        c = _camera(cam)
+        o = _opts(**opts)
+        _check(lib().vx_render(self._h, ctypes.byref(c), ctypes.c_void_p(hits.data_ptr()), layout, ctypes.byref(o),
+                               _stream_handle(stream)))
+        return hits
+
+    def render_host(self, cam: dict, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,
+                    **opts) -> np.ndarray:
+        c = _camera(cam)
+        n = int(cam["width"]) * int(cam["height"])
+        if out is None:
+            out = np.empty(n, dtype=hit_dtype(layout))
+        o = _opts(**opts)
+        _check(lib().vx_render_host(self._h, ctypes.byref(c), ctypes.c_void_p(out.ctypes.data), layout,
+                                    ctypes.byref(o), _stream_handle(stream)))
+        return out
+
+
+def raygen_pinhole(cam: dict, rays=None, stream=None):
+    """Pinhole rays on the GPU (CUDA tensor (W*H, 8) float32)."""
+    import torch
+    n = int(cam["width"]) * int(cam["height"])
+    if rays is None:
+        rays = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    c = _camera(cam)
+    _check(lib().vx_raygen_pinhole(ctypes.byref(c), ctypes.c_void_p(rays.data_ptr()), _stream_handle(stream)))
+    return rays

@@ -1,0 +1,521 @@
+// build.cpp -- host construction of a hybrid format in the paper's word-buffer
+// layout, and its inverse (decoding a cube of voxels).
+//
+// Construction follows Sec. 4.1 and Fig. 4 (construct): the function of level
+// k maps the lower corner of a sub-volume to its data; for every child cell it
+// asks level k+1 for the child's sub-volume, writes it to the buffer unless
+// it is empty (then the child pointer is 0), and stores the pointer.  Children
+// are visited in Morton order (Sec. 5, Fig. 5), so every pointer refers to
+// words already written, and the root function writes the root sub-volume
+// last and its pointer into word 0 (Sec. 4.1).
+//
+// Layout (Sec. 3.3, Fig. 3):
+//   Raw R(W,H,D): 2^(W+H+D) terminating integers, cell (x,y,z) at
+//     x + (y << W) + (z << (W+H)).
+//   SVO S(L): 2-word nodes {first-child pointer | terminating integer,
+//     valid | leaf << 8}; a node's valid children are written contiguously,
+//     2 words each, in child-index order (i = x | y << 1 | z << 2), when the
+//     node is formed; leaf children (depth L) are {terminating integer, 0}.
+//     The root node is the sub-volume's data.  This is the bottom-up
+//     construction of Baert et al. that the paper uses, written as a
+//     post-order recursion: a node is formed right after its last child,
+//     exactly when the queue-based form would form it.
+//   SVDAG G(L): nodes {valid | leaf << 8, one pointer per valid child};
+//     leaf nodes are one terminating-integer word.  When a node is formed,
+//     each child is looked up in the de-duplication map and written only if
+//     absent (Sec. 4.1); the map is per sub-volume, or shared by the whole
+//     level with VX_DEDUP_WHOLE_LEVEL (Sec. 4.3).
+// A terminating integer is the word offset of the next level's sub-volume,
+// or the voxel's RGBA at the last level; 0 is empty (Sec. 3.3).
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <unordered_map>
+
+#include "vx_internal.hpp"
+
+namespace vx {
+
+// ---------------------------------------------------------------------------
+// Dense host grid with an occupancy pyramid for empty-cube tests.
+// ---------------------------------------------------------------------------
+namespace {
+
+class DenseSource final : public VoxelSource {
+  public:
+    DenseSource(const uint32_t* w, const int ld[3]) : w_(w) {
+        for (int i = 0; i < 3; i++) { ld_[i] = ld[i]; n_[i] = (int64_t)1 << ld[i]; }
+        levels_ = std::max(ld[0], std::max(ld[1], ld[2])) + 1;
+        pyr_.resize(levels_);
+        for (int m = 0; m < levels_; m++) {
+            for (int i = 0; i < 3; i++) pn_[m][i] = std::max<int64_t>(1, n_[i] >> m);
+            pyr_[m].assign((size_t)((pn_[m][0] * pn_[m][1] * pn_[m][2] + 63) / 64), 0ull);
+        }
+        const int64_t total = n_[0] * n_[1] * n_[2];
+        for (int64_t i = 0; i < total; i++)
+            if (w_[i]) pyr_[0][(size_t)(i >> 6)] |= 1ull << (i & 63);
+        for (int m = 1; m < levels_; m++)
+            for (int64_t z = 0; z < pn_[m - 1][2]; z++)
+                for (int64_t y = 0; y < pn_[m - 1][1]; y++)
+                    for (int64_t x = 0; x < pn_[m - 1][0]; x++)
+                        if (bit(m - 1, x, y, z)) set(m, x >> 1, y >> 1, z >> 1);
+    }
+    bool empty(int64_t x0, int64_t y0, int64_t z0, int s) override {
+        if (s >= levels_) s = levels_ - 1;
+        return !bit(s, x0 >> s, y0 >> s, z0 >> s);
+    }
+    int block(int64_t x0, int64_t y0, int64_t z0, int s, uint32_t* out) override {
+        const int64_t side = (int64_t)1 << s;
+        for (int64_t z = 0; z < side; z++)
+            for (int64_t y = 0; y < side; y++)
+                memcpy(out + side * (y + side * z), w_ + x0 + n_[0] * ((y0 + y) + n_[1] * (z0 + z)),
+                       sizeof(uint32_t) * side);
+        return 0;
+    }
+
+  private:
+    bool bit(int m, int64_t x, int64_t y, int64_t z) const {
+        int64_t i = x + pn_[m][0] * (y + pn_[m][1] * z);
+        return (pyr_[m][(size_t)(i >> 6)] >> (i & 63)) & 1ull;
+    }
+    void set(int m, int64_t x, int64_t y, int64_t z) {
+        int64_t i = x + pn_[m][0] * (y + pn_[m][1] * z);
+        pyr_[m][(size_t)(i >> 6)] |= 1ull << (i & 63);
+    }
+    const uint32_t* w_;
+    int ld_[3];
+    int64_t n_[3];
+    int levels_;
+    int64_t pn_[kMaxLog2Dim + 2][3];
+    std::vector<std::vector<uint64_t>> pyr_;
+};
+
+// ---------------------------------------------------------------------------
+// Grid produced brick by brick by a callback (the lazy voxelizer of Sec. 5):
+// cubes of side 2^kBrick are fetched on demand, their emptiness remembered,
+// and the last few kept in an LRU cache.
+// ---------------------------------------------------------------------------
+class BrickSource final : public VoxelSource {
+  public:
+    explicit BrickSource(const vx_grid* g) : g_(*g) {
+        int mn = 64;
+        for (int i = 0; i < 3; i++) { ld_[i] = (int)g->log2_dim[i]; mn = std::min(mn, ld_[i]); }
+        bl_ = std::min(6, mn);
+        for (int i = 0; i < 3; i++) nb_[i] = (int64_t)1 << (ld_[i] - bl_);
+        known_.assign((size_t)(nb_[0] * nb_[1] * nb_[2]), 0);
+    }
+    bool empty(int64_t x0, int64_t y0, int64_t z0, int s) override {
+        if (g_.block_empty && g_.block_empty(g_.user, (uint32_t)x0, (uint32_t)y0, (uint32_t)z0, (uint32_t)s)) return true;
+        if (s >= bl_) {
+            const int64_t k = (int64_t)1 << (s - bl_);
+            for (int64_t bz = z0 >> bl_; bz < (z0 >> bl_) + k; bz++)
+                for (int64_t by = y0 >> bl_; by < (y0 >> bl_) + k; by++)
+                    for (int64_t bx = x0 >> bl_; bx < (x0 >> bl_) + k; bx++)
+                        if (!brick_empty(bx, by, bz)) return false;
+            return true;
+        }
+        if (brick_empty(x0 >> bl_, y0 >> bl_, z0 >> bl_)) return true;
+        const Brick* b = fetch(x0 >> bl_, y0 >> bl_, z0 >> bl_);
+        if (!b) return false;
+        const int64_t side = (int64_t)1 << s, bs = (int64_t)1 << bl_;
+        const int64_t ox = x0 & (bs - 1), oy = y0 & (bs - 1), oz = z0 & (bs - 1);
+        for (int64_t z = 0; z < side; z++)
+            for (int64_t y = 0; y < side; y++)
+                for (int64_t x = 0; x < side; x++)
+                    if (b->w[(size_t)((ox + x) + bs * ((oy + y) + bs * (oz + z)))]) return false;
+        return true;
+    }
+    int block(int64_t x0, int64_t y0, int64_t z0, int s, uint32_t* out) override {
+        const int64_t side = (int64_t)1 << s;
+        if (s >= bl_) {
+            // several bricks: copy each
+            const int64_t bs = (int64_t)1 << bl_;
+            for (int64_t bz = 0; bz < side; bz += bs)
+                for (int64_t by = 0; by < side; by += bs)
+                    for (int64_t bx = 0; bx < side; bx += bs) {
+                        const Brick* b = fetch((x0 + bx) >> bl_, (y0 + by) >> bl_, (z0 + bz) >> bl_);
+                        if (!b) return VX_EINVAL;
+                        for (int64_t z = 0; z < bs; z++)
+                            for (int64_t y = 0; y < bs; y++)
+                                memcpy(out + (bx + side * ((by + y) + side * (bz + z))), b->w.data() + bs * (y + bs * z),
+                                       sizeof(uint32_t) * bs);
+                    }
+            return 0;
+        }
+        const Brick* b = fetch(x0 >> bl_, y0 >> bl_, z0 >> bl_);
+        if (!b) return VX_EINVAL;
+        const int64_t bs = (int64_t)1 << bl_;
+        const int64_t ox = x0 & (bs - 1), oy = y0 & (bs - 1), oz = z0 & (bs - 1);
+        for (int64_t z = 0; z < side; z++)
+            for (int64_t y = 0; y < side; y++)
+                memcpy(out + side * (y + side * z), b->w.data() + (ox + bs * ((oy + y) + bs * (oz + z))),
+                       sizeof(uint32_t) * side);
+        return 0;
+    }
+    int error() const { return err_; }
+
+  private:
+    struct Brick {
+        int64_t key;
+        std::vector<uint32_t> w;
+        uint64_t stamp;
+    };
+    bool brick_empty(int64_t bx, int64_t by, int64_t bz) {
+        size_t i = (size_t)(bx + nb_[0] * (by + nb_[1] * bz));
+        if (!known_[i]) fetch(bx, by, bz);
+        return known_[i] == 1;
+    }
+    const Brick* fetch(int64_t bx, int64_t by, int64_t bz) {
+        const int64_t key = bx + nb_[0] * (by + nb_[1] * bz);
+        for (auto& b : cache_)
+            if (b.key == key) { b.stamp = ++clock_; return &b; }
+        Brick* slot = nullptr;
+        if (cache_.size() < kCache) {
+            cache_.push_back(Brick{});
+            slot = &cache_.back();
+        } else {
+            slot = &*std::min_element(cache_.begin(), cache_.end(),
+                                      [](const Brick& a, const Brick& b) { return a.stamp < b.stamp; });
+        }
+        const int64_t bs = (int64_t)1 << bl_;
+        slot->w.resize((size_t)(bs * bs * bs));
+        slot->key = key;
+        slot->stamp = ++clock_;
+        if (g_.fill_brick(g_.user, (uint32_t)(bx * bs), (uint32_t)(by * bs), (uint32_t)(bz * bs), (uint32_t)bl_,
+                          slot->w.data()) != 0) {
+            err_ = VX_EINVAL;
+            std::fill(slot->w.begin(), slot->w.end(), 0u);
+        }
+        bool any = false;
+        for (uint32_t v : slot->w)
+            if (v) { any = true; break; }
+        known_[(size_t)key] = any ? 2 : 1;
+        return slot;
+    }
+    static constexpr size_t kCache = 64;
+    vx_grid g_;
+    int ld_[3];
+    int bl_;
+    int64_t nb_[3];
+    std::vector<uint8_t> known_;  // 0 unknown, 1 empty, 2 occupied
+    std::vector<Brick> cache_;
+    uint64_t clock_ = 0;
+    int err_ = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Builder
+// ---------------------------------------------------------------------------
+struct NodeKey {
+    uint32_t n;
+    uint32_t w[9];
+    bool operator==(const NodeKey& o) const {
+        if (n != o.n) return false;
+        for (uint32_t i = 0; i < n; i++)
+            if (w[i] != o.w[i]) return false;
+        return true;
+    }
+};
+struct NodeKeyHash {
+    size_t operator()(const NodeKey& k) const {
+        uint64_t h = 0x9E3779B97F4A7C15ull ^ k.n;
+        for (uint32_t i = 0; i < k.n; i++) {
+            h ^= k.w[i];
+            h *= 0xBF58476D1CE4E5B9ull;
+            h ^= h >> 29;
+        }
+        return (size_t)h;
+    }
+};
+
+class Builder {
+  public:
+    Builder(const Spec& sp, VoxelSource& src, int scope, BuildResult& R) : sp_(sp), src_(src), scope_(scope), R_(R) {
+        nlev_ = (int)sp.lv.size();
+        int acc = 0;
+        for (int k = nlev_ - 1; k >= 0; k--) {
+            s_[k] = acc;  // cell side of level k (cubic below the top level)
+            acc += sp.lv[k].e[0];
+        }
+        maps_.resize(nlev_);
+        for (int i = 0; i < 3; i++) cb_[i] = std::min(5, sp.ldim[i]);
+        cside_ = std::min(cb_[0], std::min(cb_[1], cb_[2]));
+        cache_.resize((size_t)1 << (3 * cside_));
+    }
+
+    int run() {
+        R_.words.assign(1, 0u);
+        std::vector<uint32_t> data;
+        const int64_t lo[3] = {0, 0, 0};
+        if (construct(0, lo, data)) {
+            uint32_t p = write(0, data.data(), data.size());
+            if (!err_) R_.words[0] = p;
+        }
+        return err_;
+    }
+
+  private:
+    uint32_t write(int k, const uint32_t* w, size_t n) {
+        if (R_.words.size() + n > 0xFFFFFFFFull) {
+            err_ = fail(VX_ETOOBIG, "format buffer exceeds 2^32 words (16 GiB, Sec. 3.3)");
+            return 0;
+        }
+        uint32_t off = (uint32_t)R_.words.size();
+        R_.words.insert(R_.words.end(), w, w + n);
+        R_.level_words[k] += n;
+        return off;
+    }
+
+    uint32_t voxel(const int64_t v[3]) {
+        const int64_t m = (int64_t)1 << cside_;
+        const int64_t c[3] = {v[0] & ~(m - 1), v[1] & ~(m - 1), v[2] & ~(m - 1)};
+        if (!cache_valid_ || c[0] != corner_[0] || c[1] != corner_[1] || c[2] != corner_[2]) {
+            if (src_.block(c[0], c[1], c[2], cside_, cache_.data()) != 0)
+                err_ = fail(VX_EINVAL, "voxel source failed for brick at (%lld,%lld,%lld)", (long long)c[0],
+                            (long long)c[1], (long long)c[2]);
+            corner_[0] = c[0]; corner_[1] = c[1]; corner_[2] = c[2];
+            cache_valid_ = true;
+        }
+        uint32_t w = cache_[(size_t)((v[0] - c[0]) + m * ((v[1] - c[1]) + m * (v[2] - c[2])))];
+        if (w) R_.occupied++;
+        return w;
+    }
+
+    // Terminating integer of the level-k cell with lower corner lo.
+    uint32_t cell_term(int k, const int64_t lo[3]) {
+        if (k == nlev_ - 1) return voxel(lo);
+        if (src_.empty(lo[0], lo[1], lo[2], s_[k])) return 0;
+        std::vector<uint32_t> data;
+        if (!construct(k + 1, lo, data)) return 0;
+        return write(k + 1, data.data(), data.size());
+    }
+
+    // Sub-volume of level k at lo; false if it is empty.
+    bool construct(int k, const int64_t lo[3], std::vector<uint32_t>& data) {
+        if (err_) return false;
+        const Level& L = sp_.lv[k];
+        if (L.kind == K_RAW) {
+            const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
+            data.assign((size_t)cells, 0u);
+            bool any = false;
+            for (uint64_t m = 0; m < cells && !err_; m++) {
+                uint32_t c[3];
+                morton_decode(m, L.e, c);
+                const int64_t cl[3] = {lo[0] + ((int64_t)c[0] << s_[k]), lo[1] + ((int64_t)c[1] << s_[k]),
+                                       lo[2] + ((int64_t)c[2] << s_[k])};
+                uint32_t t = cell_term(k, cl);
+                data[(size_t)(c[0] + ((uint64_t)c[1] << L.e[0]) + ((uint64_t)c[2] << (L.e[0] + L.e[1])))] = t;
+                any |= t != 0;
+            }
+            if (any) R_.level_nodes[k]++;
+            return any && !err_;
+        }
+        if (L.kind == K_DAG && scope_ == VX_DEDUP_PER_SUBVOLUME) maps_[k].clear();
+        NodeKey root;
+        bool ok = (L.kind == K_SVO) ? svo_node(k, lo, 0, root) : dag_node(k, lo, 0, root);
+        if (!ok || err_) return false;
+        data.assign(root.w, root.w + root.n);
+        R_.level_nodes[k]++;
+        return true;
+    }
+
+    // Octree node of format level k at depth `depth` (0 = root, L = leaf).
+    bool svo_node(int k, const int64_t lo[3], int depth, NodeKey& out) {
+        const int L = sp_.lv[k].e[0];
+        const int side = s_[k] + L - depth;
+        if (depth == L) {
+            uint32_t t = cell_term(k, lo);
+            if (!t) return false;
+            out.n = 2; out.w[0] = t; out.w[1] = 0;
+            return true;
+        }
+        if (side > 0 && src_.empty(lo[0], lo[1], lo[2], side)) return false;
+        NodeKey ch[8];
+        uint32_t valid = 0;
+        for (int i = 0; i < 8 && !err_; i++) {
+            const int64_t h = (int64_t)1 << (side - 1);
+            const int64_t cl[3] = {lo[0] + (i & 1) * h, lo[1] + ((i >> 1) & 1) * h, lo[2] + ((i >> 2) & 1) * h};
+            if (svo_node(k, cl, depth + 1, ch[i])) valid |= 1u << i;
+        }
+        if (!valid || err_) return false;
+        uint32_t buf[16];
+        uint32_t n = 0;
+        for (int i = 0; i < 8; i++)
+            if ((valid >> i) & 1u) { buf[n++] = ch[i].w[0]; buf[n++] = ch[i].w[1]; }
+        const uint32_t first = write(k, buf, n);
+        R_.level_nodes[k] += n / 2;
+        const uint32_t leaf = (depth + 1 == L) ? valid : 0u;
+        out.n = 2; out.w[0] = first; out.w[1] = valid | (leaf << 8);
+        return true;
+    }
+
+    bool dag_node(int k, const int64_t lo[3], int depth, NodeKey& out) {
+        const int L = sp_.lv[k].e[0];
+        const int side = s_[k] + L - depth;
+        if (depth == L) {
+            uint32_t t = cell_term(k, lo);
+            if (!t) return false;
+            out.n = 1; out.w[0] = t;
+            return true;
+        }
+        if (side > 0 && src_.empty(lo[0], lo[1], lo[2], side)) return false;
+        NodeKey ch[8];
+        uint32_t valid = 0;
+        for (int i = 0; i < 8 && !err_; i++) {
+            const int64_t h = (int64_t)1 << (side - 1);
+            const int64_t cl[3] = {lo[0] + (i & 1) * h, lo[1] + ((i >> 1) & 1) * h, lo[2] + ((i >> 2) & 1) * h};
+            if (dag_node(k, cl, depth + 1, ch[i])) valid |= 1u << i;
+        }
+        if (!valid || err_) return false;
+        const uint32_t leaf = (depth + 1 == L) ? valid : 0u;
+        out.n = 1;
+        out.w[0] = valid | (leaf << 8);
+        auto& map = maps_[k];
+        for (int i = 0; i < 8; i++) {
+            if (!((valid >> i) & 1u)) continue;
+            auto it = map.find(ch[i]);
+            uint32_t p;
+            if (it != map.end()) {
+                p = it->second;
+            } else {
+                p = write(k, ch[i].w, ch[i].n);
+                R_.level_nodes[k]++;
+                map.emplace(ch[i], p);
+            }
+            out.w[out.n++] = p;
+        }
+        return true;
+    }
+
+    const Spec& sp_;
+    VoxelSource& src_;
+    int scope_;
+    BuildResult& R_;
+    int nlev_;
+    int s_[kMaxFormatLevels];
+    std::vector<std::unordered_map<NodeKey, uint32_t, NodeKeyHash>> maps_;
+    int cb_[3];
+    int cside_;
+    std::vector<uint32_t> cache_;
+    int64_t corner_[3] = {0, 0, 0};
+    bool cache_valid_ = false;
+    int err_ = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Decoder: walks the buffer like the intersection functions do, visiting only
+// children that overlap the requested cube.
+// ---------------------------------------------------------------------------
+class Decoder {
+  public:
+    Decoder(const Spec& sp, const uint32_t* w, uint64_t nw, const int64_t c0[3], int log2s, uint32_t* out)
+        : sp_(sp), w_(w), nw_(nw), out_(out) {
+        nlev_ = (int)sp.lv.size();
+        int acc = 0;
+        for (int k = nlev_ - 1; k >= 0; k--) { s_[k] = acc; acc += sp.lv[k].e[0]; }
+        side_ = (int64_t)1 << log2s;
+        for (int i = 0; i < 3; i++) c0_[i] = c0[i];
+    }
+    int run() {
+        if (nw_ < 1) return fail(VX_EINVAL, "empty buffer");
+        if (w_[0] == 0) return VX_OK;
+        const int64_t lo[3] = {0, 0, 0};
+        level(0, w_[0], lo);
+        return err_;
+    }
+
+  private:
+    bool overlaps(const int64_t lo[3], int64_t size) const {
+        for (int i = 0; i < 3; i++)
+            if (lo[i] + size <= c0_[i] || lo[i] >= c0_[i] + side_) return false;
+        return true;
+    }
+    bool in(uint64_t p, uint64_t n) {
+        if (p == 0 || p + n > nw_) { err_ = fail(VX_EINVAL, "pointer %llu out of range", (unsigned long long)p); return false; }
+        return true;
+    }
+    void emit(int k, uint32_t term, const int64_t lo[3]) {
+        if (k == nlev_ - 1) {
+            out_[(size_t)((lo[0] - c0_[0]) + side_ * ((lo[1] - c0_[1]) + side_ * (lo[2] - c0_[2])))] = term;
+        } else {
+            level(k + 1, term, lo);
+        }
+    }
+    void level(int k, uint32_t p, const int64_t lo[3]) {
+        if (err_) return;
+        const Level& L = sp_.lv[k];
+        const int64_t cs = (int64_t)1 << s_[k];
+        if (L.kind == K_RAW) {
+            const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
+            if (!in(p, cells)) return;
+            for (int64_t z = 0; z < (1 << L.e[2]); z++)
+                for (int64_t y = 0; y < (1 << L.e[1]); y++)
+                    for (int64_t x = 0; x < (1 << L.e[0]); x++) {
+                        const int64_t cl[3] = {lo[0] + x * cs, lo[1] + y * cs, lo[2] + z * cs};
+                        if (!overlaps(cl, cs)) continue;
+                        uint32_t t = w_[p + x + (y << L.e[0]) + (z << (L.e[0] + L.e[1]))];
+                        if (t) emit(k, t, cl);
+                        if (err_) return;
+                    }
+        } else {
+            node(k, p, 0, lo);
+        }
+    }
+    void node(int k, uint32_t p, int depth, const int64_t lo[3]) {
+        if (err_) return;
+        const Level& L = sp_.lv[k];
+        const bool svo = L.kind == K_SVO;
+        if (!in(p, svo ? 2 : 1)) return;
+        const uint32_t masks = svo ? w_[p + 1] : w_[p];
+        const uint32_t valid = masks & 0xFFu;
+        const int64_t half = (int64_t)1 << (s_[k] + L.e[0] - depth - 1);
+        uint32_t rank = 0;
+        for (int i = 0; i < 8; i++) {
+            if (!((valid >> i) & 1u)) continue;
+            const uint32_t r = rank++;
+            const int64_t cl[3] = {lo[0] + (i & 1) * half, lo[1] + ((i >> 1) & 1) * half, lo[2] + ((i >> 2) & 1) * half};
+            if (!overlaps(cl, half)) continue;
+            uint64_t cp;
+            if (svo) {
+                cp = (uint64_t)w_[p] + 2ull * r;
+                if (!in(cp, 2)) return;
+            } else {
+                if (!in(p + 1 + r, 1)) return;
+                cp = w_[p + 1 + r];
+                if (!in(cp, 1)) return;
+            }
+            if (depth + 1 == L.e[0]) emit(k, w_[cp], cl);
+            else node(k, (uint32_t)cp, depth + 1, cl);
+            if (err_) return;
+        }
+    }
+    const Spec& sp_;
+    const uint32_t* w_;
+    uint64_t nw_;
+    uint32_t* out_;
+    int nlev_;
+    int s_[kMaxFormatLevels];
+    int64_t side_;
+    int64_t c0_[3];
+    int err_ = 0;
+};
+
+}  // namespace
+
+VoxelSource* make_dense_source(const uint32_t* words, const int ldim[3]) { return new DenseSource(words, ldim); }
+VoxelSource* make_brick_source(const vx_grid* g) { return new BrickSource(g); }
+
+int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out) {
+    Builder b(spec, src, dedup_scope, *out);
+    return b.run();
+}
+
+int decode_cube(const Spec& spec, const uint32_t* words, uint64_t nwords, int64_t x0, int64_t y0, int64_t z0,
+                int log2s, uint32_t* out) {
+    const int64_t c0[3] = {x0, y0, z0};
+    Decoder d(spec, words, nwords, c0, log2s, out);
+    return d.run();
+}
+
+}  // namespace vx

@@ -1,0 +1,313 @@
+// capi.cpp -- the extern "C" entry points declared in include/vx.h.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <chrono>
+#include <memory>
+
+#include "vx_internal.hpp"
+
+using namespace vx;
+
+struct vx_volume_s {
+    Volume v;
+};
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? VX_ENOMEM : VX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the volume's device current for the scope of a call.
+class DeviceScope {
+  public:
+    explicit DeviceScope(int dev) {
+        cudaGetDevice(&prev_);
+        if (dev >= 0 && dev != prev_) {
+            err_ = cudaSetDevice(dev);
+            changed_ = err_ == cudaSuccess;
+        }
+    }
+    ~DeviceScope() {
+        if (changed_) cudaSetDevice(prev_);
+    }
+    cudaError_t error() const { return err_; }
+
+  private:
+    int prev_ = 0;
+    bool changed_ = false;
+    cudaError_t err_ = cudaSuccess;
+};
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_trace_args(vx_volume v, const void* rays, uint64_t n, const void* hits, int32_t layout) {
+    if (!v) return fail(VX_EINVAL, "volume is NULL");
+    if (!v->v.d_pool) return fail(VX_EINVAL, "volume has no device image (built with no_upload)");
+    if (layout != VX_HIT_FULL && layout != VX_HIT_COMPACT) return fail(VX_EINVAL, "bad hit layout %d", layout);
+    if (layout == VX_HIT_COMPACT && v->v.spec.ldim[0] + v->v.spec.ldim[1] + v->v.spec.ldim[2] >= 32)
+        return fail(VX_EINVAL, "compact hits need fewer than 2^32 voxels");
+    if (n == 0) return VX_OK;
+    if (rays && !aligned(rays, 16)) return fail(VX_EINVAL, "rays must be 16-byte aligned");
+    if (!hits) return fail(VX_EINVAL, "hits is NULL");
+    if (!aligned(hits, layout == VX_HIT_FULL ? 16 : 8)) return fail(VX_EINVAL, "hits misaligned for the layout");
+    return VX_OK;
+}
+
+size_t hit_bytes(int layout) { return layout == VX_HIT_FULL ? sizeof(vx_hit) : sizeof(vx_hit_compact); }
+
+int ensure_staging(Volume& V) {
+    Staging& S = V.staging;
+    if (S.ready) return VX_OK;
+    for (int i = 0; i < 2; i++) {
+        cudaError_t e = cudaMalloc(&S.d_rays[i], Staging::kChunk * sizeof(vx_ray));
+        if (e) return cuda_fail(e, "cudaMalloc (staging rays)");
+        e = cudaMalloc(&S.d_hits[i], Staging::kChunk * sizeof(vx_hit));
+        if (e) return cuda_fail(e, "cudaMalloc (staging hits)");
+        cudaStream_t st;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e) return cuda_fail(e, "cudaStreamCreate");
+        S.streams[i] = st;
+    }
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e) return cuda_fail(e, "cudaEventCreate");
+    S.ready = ev;
+    return VX_OK;
+}
+
+void free_staging(Staging& S) {
+    for (int i = 0; i < 2; i++) {
+        if (S.d_rays[i]) cudaFree(S.d_rays[i]);
+        if (S.d_hits[i]) cudaFree(S.d_hits[i]);
+        if (S.streams[i]) cudaStreamDestroy((cudaStream_t)S.streams[i]);
+        S.d_rays[i] = S.d_hits[i] = S.streams[i] = nullptr;
+    }
+    if (S.ready) cudaEventDestroy((cudaEvent_t)S.ready);
+    S.ready = nullptr;
+}
+
+// Runs `work(k, i0, n, d_rays, d_hits, stream)` over chunks of the input on
+// two streams, so the copies of one chunk overlap the kernel of the other.
+template <class Work>
+int pipeline(Volume& V, uint64_t n, void* stream, Work work) {
+    std::lock_guard<std::mutex> lock(V.staging_mu);
+    int rc = ensure_staging(V);
+    if (rc) return rc;
+    Staging& S = V.staging;
+    cudaEvent_t ready = (cudaEvent_t)S.ready;
+    cudaError_t e = cudaEventRecord(ready, (cudaStream_t)stream);
+    if (e) return cuda_fail(e, "cudaEventRecord");
+    for (int i = 0; i < 2; i++) {
+        e = cudaStreamWaitEvent((cudaStream_t)S.streams[i], ready, 0);
+        if (e) return cuda_fail(e, "cudaStreamWaitEvent");
+    }
+    uint64_t k = 0;
+    for (uint64_t i0 = 0; i0 < n; i0 += Staging::kChunk, k++) {
+        const uint64_t m = (n - i0) < Staging::kChunk ? (n - i0) : Staging::kChunk;
+        const int b = (int)(k & 1);
+        rc = work(i0, m, S.d_rays[b], S.d_hits[b], (cudaStream_t)S.streams[b]);
+        if (rc) break;
+    }
+    for (int i = 0; i < 2; i++) {
+        e = cudaStreamSynchronize((cudaStream_t)S.streams[i]);
+        if (e && !rc) rc = cuda_fail(e, "trace pipeline");
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_opts* opts, vx_volume* out) {
+    clear_error();
+    if (!out) return fail(VX_EINVAL, "out is NULL");
+    *out = nullptr;
+    Spec sp;
+    int rc = parse_spec(spec, &sp);
+    if (rc) return rc;
+    if (!grid) return fail(VX_EINVAL, "grid is NULL");
+    if ((grid->dense != nullptr) == (grid->fill_brick != nullptr))
+        return fail(VX_EINVAL, "set exactly one of grid->dense and grid->fill_brick");
+    for (int i = 0; i < 3; i++)
+        if ((int)grid->log2_dim[i] != sp.ldim[i])
+            return fail(VX_EINVAL, "spec '%s' describes a 2^%d x 2^%d x 2^%d grid, the grid is 2^%u x 2^%u x 2^%u",
+                        spec, sp.ldim[0], sp.ldim[1], sp.ldim[2], grid->log2_dim[0], grid->log2_dim[1],
+                        grid->log2_dim[2]);
+    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0};
+    if (opts) o = *opts;
+    if (o.dedup_scope != VX_DEDUP_WHOLE_LEVEL && o.dedup_scope != VX_DEDUP_PER_SUBVOLUME)
+        return fail(VX_EINVAL, "bad dedup_scope %d", o.dedup_scope);
+
+    std::unique_ptr<vx_volume_s> h(new vx_volume_s);
+    Volume& V = h->v;
+    V.spec = sp;
+    const double t0 = now_ms();
+    std::unique_ptr<VoxelSource> src(grid->dense ? make_dense_source(grid->dense, sp.ldim) : make_brick_source(grid));
+    rc = build_canonical(sp, *src, o.dedup_scope, &V.built);
+    if (rc) return rc;
+    const double t1 = now_ms();
+
+    vx_stats& st = V.stats;
+    memset(&st, 0, sizeof st);
+    st.n_levels = (uint32_t)sp.lv.size();
+    st.n_node_levels = sp.fmt.J;
+    for (int i = 0; i < 3; i++) st.log2_dim[i] = (uint32_t)sp.ldim[i];
+    st.canonical_words = V.built.words.size();
+    st.occupied_voxels = V.built.occupied;
+    for (int k = 0; k < VX_MAX_LEVELS; k++) {
+        st.level_words[k] = V.built.level_words[k];
+        st.level_nodes[k] = V.built.level_nodes[k];
+    }
+    st.build_ms = t1 - t0;
+    V.kernels = kernels_for(sp);
+    st.specialized = kernel_set_specialized(V.kernels) ? 1 : 0;
+
+    if (!o.no_upload) {
+        int dev = o.device;
+        if (dev < 0) {
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e) return cuda_fail(e, "cudaGetDevice");
+        }
+        DeviceScope ds(dev);
+        if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+        V.device = dev;
+        const uint64_t bytes = V.built.words.size() * sizeof(uint32_t);
+        cudaError_t e = cudaMalloc((void**)&V.d_pool, bytes);
+        if (e) return cuda_fail(e, "cudaMalloc (device image)");
+        e = cudaMemcpy(V.d_pool, V.built.words.data(), bytes, cudaMemcpyHostToDevice);
+        if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
+        V.pool_words = V.built.words.size();
+        st.device_bytes = bytes;
+        st.upload_ms = now_ms() - t1;
+    }
+    *out = h.release();
+    return VX_OK;
+}
+
+extern "C" int vx_free(vx_volume v) {
+    clear_error();
+    if (!v) return VX_OK;
+    {
+        DeviceScope ds(v->v.device);
+        if (v->v.d_pool) {
+            cudaDeviceSynchronize();
+            cudaFree(v->v.d_pool);
+        }
+        free_staging(v->v.staging);
+    }
+    delete v;
+    return VX_OK;
+}
+
+extern "C" int vx_stats_get(vx_volume v, vx_stats* out) {
+    clear_error();
+    if (!v || !out) return fail(VX_EINVAL, "NULL argument");
+    *out = v->v.stats;
+    return VX_OK;
+}
+
+extern "C" int vx_canonical(vx_volume v, const uint32_t** words, uint64_t* n_words) {
+    clear_error();
+    if (!v || !words || !n_words) return fail(VX_EINVAL, "NULL argument");
+    *words = v->v.built.words.data();
+    *n_words = v->v.built.words.size();
+    return VX_OK;
+}
+
+extern "C" int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t log2_size, uint32_t* out) {
+    clear_error();
+    if (!v || !out) return fail(VX_EINVAL, "NULL argument");
+    const Spec& sp = v->v.spec;
+    const uint32_t c[3] = {x0, y0, z0};
+    for (int i = 0; i < 3; i++) {
+        if ((int)log2_size > sp.ldim[i]) return fail(VX_EINVAL, "cube larger than the grid");
+        if (c[i] & ((1u << log2_size) - 1u)) return fail(VX_EINVAL, "cube corner not a multiple of its side");
+        if ((uint64_t)c[i] + (1ull << log2_size) > (1ull << sp.ldim[i])) return fail(VX_EINVAL, "cube outside the grid");
+    }
+    memset(out, 0, sizeof(uint32_t) << (3 * log2_size));
+    return decode_cube(sp, v->v.built.words.data(), v->v.built.words.size(), x0, y0, z0, (int)log2_size, out);
+}
+
+extern "C" int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
+                        const vx_trace_opts* opts, void* stream) {
+    clear_error();
+    int rc = check_trace_args(v, rays, n, hits, hit_layout);
+    if (rc || n == 0) return rc;
+    if (!rays) return fail(VX_EINVAL, "rays is NULL");
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return launch_trace(v->v, rays, n, hits, hit_layout, opts, stream);
+}
+
+extern "C" int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,
+                             const vx_trace_opts* opts, void* stream) {
+    clear_error();
+    int rc = check_trace_args(v, rays_host, n, hits_host, hit_layout);
+    if (rc || n == 0) return rc;
+    if (!rays_host) return fail(VX_EINVAL, "rays is NULL");
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    const size_t hb = hit_bytes(hit_layout);
+    Volume& V = v->v;
+    return pipeline(V, n, stream, [&](uint64_t i0, uint64_t m, void* dr, void* dh, cudaStream_t st) {
+        cudaError_t e = cudaMemcpyAsync(dr, rays_host + i0, m * sizeof(vx_ray), cudaMemcpyHostToDevice, st);
+        if (e) return cuda_fail(e, "cudaMemcpyAsync (rays)");
+        int r = launch_trace(V, (const vx_ray*)dr, m, dh, hit_layout, opts, st);
+        if (r) return r;
+        e = cudaMemcpyAsync((char*)hits_host + i0 * hb, dh, m * hb, cudaMemcpyDeviceToHost, st);
+        if (e) return cuda_fail(e, "cudaMemcpyAsync (hits)");
+        return (int)VX_OK;
+    });
+}
+
+extern "C" int vx_raygen_pinhole(const vx_camera* cam, vx_ray* rays, void* stream) {
+    clear_error();
+    CameraParams cp;
+    int rc = camera_params(cam, &cp);
+    if (rc) return rc;
+    if (!rays) return fail(VX_EINVAL, "rays is NULL");
+    if (!aligned(rays, 16)) return fail(VX_EINVAL, "rays must be 16-byte aligned");
+    return launch_raygen(cp, rays, stream);
+}
+
+extern "C" int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t hit_layout, const vx_trace_opts* opts,
+                         void* stream) {
+    clear_error();
+    CameraParams cp;
+    int rc = camera_params(cam, &cp);
+    if (rc) return rc;
+    const uint64_t n = (uint64_t)cp.W * cp.H;
+    rc = check_trace_args(v, nullptr, n, hits, hit_layout);
+    if (rc) return rc;
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return launch_render(v->v, cp, 0, n, hits, hit_layout, opts, stream);
+}
+
+extern "C" int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host, int32_t hit_layout,
+                              const vx_trace_opts* opts, void* stream) {
+    clear_error();
+    CameraParams cp;
+    int rc = camera_params(cam, &cp);
+    if (rc) return rc;
+    const uint64_t n = (uint64_t)cp.W * cp.H;
+    rc = check_trace_args(v, nullptr, n, hits_host, hit_layout);
+    if (rc) return rc;
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    const size_t hb = hit_bytes(hit_layout);
+    Volume& V = v->v;
+    return pipeline(V, n, stream, [&](uint64_t i0, uint64_t m, void*, void* dh, cudaStream_t st) {
+        int r = launch_render(V, cp, i0, m, dh, hit_layout, opts, st);
+        if (r) return r;
+        cudaError_t e = cudaMemcpyAsync((char*)hits_host + i0 * hb, dh, m * hb, cudaMemcpyDeviceToHost, st);
+        if (e) return cuda_fail(e, "cudaMemcpyAsync (hits)");
+        return (int)VX_OK;
+    });
+}

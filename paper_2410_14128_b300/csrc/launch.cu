@@ -1,0 +1,122 @@
+// launch.cu -- kernel registry, the run-time-described kernel set, camera set-up
+// and the pinhole ray generator.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "trace.cuh"
+#include "vx_internal.hpp"
+
+namespace vx {
+
+namespace {
+std::vector<const KernelSet*>& registry() {
+    static std::vector<const KernelSet*> r;
+    return r;
+}
+const KernelSet g_generic = {"*", false, FmtParams{}, &Launch<DynF>::trace, &Launch<DynF>::render};
+
+CamDev to_dev(const CameraParams& c) {
+    CamDev d;
+    for (int i = 0; i < 3; i++) { d.eye[i] = c.eye[i]; d.f[i] = c.f[i]; d.r[i] = c.r[i]; d.u[i] = c.u[i]; }
+    d.tha = c.tha; d.th = c.th; d.W = c.W; d.H = c.H;
+    return d;
+}
+
+int pick_block(const vx_trace_opts* o) {
+    int b = (o && o->block > 0) ? o->block : 256;
+    return b;
+}
+
+__global__ void __launch_bounds__(256) k_raygen(CamDev cam, float4* __restrict__ rays) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (uint64_t)cam.W * cam.H) return;
+    const RayIn r = pinhole_ray(cam, (uint32_t)(i % cam.W), (uint32_t)(i / cam.W));
+    __stcs(rays + 2 * i, make_float4(r.o[0], r.o[1], r.o[2], r.tmin));
+    __stcs(rays + 2 * i + 1, make_float4(r.d[0], r.d[1], r.d[2], r.tmax));
+}
+}  // namespace
+
+void register_kernel_set(const KernelSet* ks) { registry().push_back(ks); }
+
+const KernelSet* find_kernels(const std::string& spec) {
+    for (const KernelSet* k : registry())
+        if (spec == k->spec) return k;
+    return nullptr;
+}
+
+const KernelSet* generic_kernels() { return &g_generic; }
+
+bool kernel_set_specialized(const KernelSet* k) { return k && k->specialized; }
+
+static bool same_params(const FmtParams& a, const FmtParams& b) { return memcmp(&a, &b, sizeof(FmtParams)) == 0; }
+
+const KernelSet* kernels_for(const Spec& sp) {
+    const KernelSet* k = find_kernels(sp.canonical);
+    if (k && same_params(k->params, sp.fmt)) return k;
+    return generic_kernels();
+}
+
+int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
+                 void* stream) {
+    const int block = pick_block(o);
+    int e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout, block,
+                             (cudaStream_t)stream);
+    if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return VX_OK;
+}
+
+int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
+                  const vx_trace_opts* o, void* stream) {
+    const int block = pick_block(o);
+    int e = v.kernels->render(v.spec.fmt, v.d_pool, to_dev(cp), i0, n, hits, layout, block, (cudaStream_t)stream);
+    if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return VX_OK;
+}
+
+int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream) {
+    const uint64_t n = (uint64_t)cp.W * cp.H;
+    if (n == 0) return VX_OK;
+    k_raygen<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(to_dev(cp), reinterpret_cast<float4*>(rays));
+    cudaError_t e = cudaGetLastError();
+    if (e) return fail(VX_ECUDA, "raygen launch failed: %s", cudaGetErrorString(e));
+    return VX_OK;
+}
+
+// Camera basis in FP64 on the host, handed to the kernels in FP32.
+int camera_params(const vx_camera* cam, CameraParams* out) {
+    if (!cam) return fail(VX_EINVAL, "camera is NULL");
+    if (cam->width == 0 || cam->height == 0) return fail(VX_EINVAL, "camera has an empty image");
+    if (!(cam->vfov_deg > 0.0 && cam->vfov_deg < 180.0)) return fail(VX_EINVAL, "vfov must be in (0, 180)");
+    double f[3], r[3], u[3];
+    for (int i = 0; i < 3; i++) f[i] = cam->look[i] - cam->eye[i];
+    double lf = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(lf > 0.0)) return fail(VX_EINVAL, "camera eye and look coincide");
+    for (int i = 0; i < 3; i++) f[i] /= lf;
+    const double* up = cam->up;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    double lr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(lr > 0.0)) return fail(VX_EINVAL, "camera up is parallel to the view direction");
+    for (int i = 0; i < 3; i++) r[i] /= lr;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    const double th = tan(cam->vfov_deg * 3.14159265358979323846 / 360.0);
+    for (int i = 0; i < 3; i++) {
+        out->eye[i] = (float)cam->eye[i];
+        out->f[i] = (float)f[i];
+        out->r[i] = (float)r[i];
+        out->u[i] = (float)u[i];
+    }
+    out->th = (float)th;
+    out->tha = (float)(th * (double)cam->width / (double)cam->height);
+    out->W = cam->width;
+    out->H = cam->height;
+    return VX_OK;
+}
+
+}  // namespace vx

@@ -1,0 +1,585 @@
+// trace.cuh -- first-hit traversal of a hybrid voxel format on sm_103a.
+//
+// What it computes (Sec. 4.2): the root function reads the root pointer from
+// word 0, tests the ray against the root box and enters level 1; each level
+// visits the non-empty children its ray crosses in hit-time order and hands
+// the first non-empty one to the next level (Fig. 4, intersect /
+// ordered_hit_children); the answer is the first occupied voxel.
+//
+// How (a B300 design, not the paper's GLSL):
+//   * All levels share one loop.  The format is expanded into node levels
+//     (fmt.hpp); the ray keeps the integer coordinate of the cell it is in
+//     at the current node level, and a short stack of node pointers, one per
+//     level.  Each iteration either looks the current cell up (and descends
+//     into it when it is non-empty) or takes one Amanatides-Woo step to the
+//     neighbouring cell of the same level (Sec. 2; Raw levels are a plain
+//     grid DDA, octree nodes are a 2x2x2 grid), so lanes of a warp execute
+//     the same instructions whatever level each is at.  Stepping out of a
+//     node resumes at the deepest ancestor that still contains the new cell
+//     (the highest changed coordinate bit selects it), so no level ever
+//     re-walks its parent.
+//   * Raw lookups read cell x + (y << W) + (z << (W+H)); octree children are
+//     found from the valid mask with popc: the child list of an SVO node is
+//     contiguous (first + 2 rank), an SVDAG node lists one pointer per valid
+//     child (node[1 + rank]) (Sec. 3.3, Fig. 3).
+//   * Every boundary crossing is computed in closed form from the integer
+//     plane, t = (plane - o) / d, in FP32.  Whenever two FP32 quantities that
+//     decide a step lie within 2^-20 (relative) of each other -- 16x the
+//     worst FP32 error of those expressions -- the decision is re-taken in
+//     FP64 with exactly the expressions of the FP64 reference stepper
+//     (lowest axis first on equality).  So the voxel found equals that of a
+//     plain FP64 DDA over the uncompressed grid, not just within a tolerance.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmt.hpp"
+
+namespace vx {
+
+constexpr float kGuard = 9.5367431640625e-07f;  // 2^-20
+constexpr int kIterCap = 1 << 22;
+
+enum : uint32_t { ST_MISS = 0, ST_HIT = 1, ST_INVALID = 2, ST_ERROR = 3 };
+
+// ---------------------------------------------------------------------------
+// Format accessors: run-time (kernel argument) and compile-time (template).
+// ---------------------------------------------------------------------------
+struct DynF {
+    FmtParams p;
+    static constexpr int kMaxJ = kMaxNodeLevels;
+    __device__ __forceinline__ int J() const { return (int)p.J; }
+    __device__ __forceinline__ int kind(int j) const { return (int)((p.kind >> (2 * j)) & 3u); }
+    __device__ __forceinline__ int s(int j) const { return (int)((p.s >> (4 * j)) & 15u); }
+    __device__ __forceinline__ int b(int j) const { return (int)((p.b >> (4 * j)) & 15u); }
+    __device__ __forceinline__ bool bot(int j) const { return (p.bot >> j) & 1u; }
+    __device__ __forceinline__ int b0(int a) const { return (int)p.b0[a]; }
+    __device__ __forceinline__ int ldim(int a) const { return (int)p.ldim[a]; }
+    __device__ __forceinline__ int jpop(int h) const { return (int)((p.jpop >> (4 * h)) & 15u); }
+    __device__ __forceinline__ bool has_svo() const { return true; }
+    __device__ __forceinline__ bool has_dag() const { return true; }
+};
+
+template <uint32_t J_, uint32_t KIND, uint32_t BOT, uint64_t S, uint64_t B, uint32_t B0X, uint32_t B0Y, uint32_t B0Z,
+          uint32_t LX, uint32_t LY, uint32_t LZ, uint64_t JPOP>
+struct StatF {
+    static constexpr int kMaxJ = (int)J_;
+    __device__ __forceinline__ int J() const { return (int)J_; }
+    __device__ __forceinline__ int kind(int j) const { return (int)((KIND >> (2 * j)) & 3u); }
+    __device__ __forceinline__ int s(int j) const { return (int)((S >> (4 * j)) & 15u); }
+    __device__ __forceinline__ int b(int j) const { return (int)((B >> (4 * j)) & 15u); }
+    __device__ __forceinline__ bool bot(int j) const { return (BOT >> j) & 1u; }
+    __device__ __forceinline__ int b0(int a) const { return (int)(a == 0 ? B0X : (a == 1 ? B0Y : B0Z)); }
+    __device__ __forceinline__ int ldim(int a) const { return (int)(a == 0 ? LX : (a == 1 ? LY : LZ)); }
+    __device__ __forceinline__ int jpop(int h) const { return (int)((JPOP >> (4 * h)) & 15u); }
+    static constexpr bool kHasSvo = (KIND & 0x55555555u & ~(KIND >> 1)) != 0;
+    static constexpr bool kHasDag = ((KIND >> 1) & 0x55555555u & ~KIND) != 0;
+    __device__ __forceinline__ bool has_svo() const { return kHasSvo; }
+    __device__ __forceinline__ bool has_dag() const { return kHasDag; }
+};
+
+// Compile-time composition: Format<Raw<4,4,4>, Svo<2>, Dag<3>>.
+template <int W, int H, int D>
+struct Raw {
+    static constexpr LevelDesc desc() { return LevelDesc{K_RAW, {W, H, D}}; }
+};
+template <int L>
+struct Svo {
+    static constexpr LevelDesc desc() { return LevelDesc{K_SVO, {L, L, L}}; }
+};
+template <int L>
+struct Dag {
+    static constexpr LevelDesc desc() { return LevelDesc{K_DAG, {L, L, L}}; }
+};
+
+template <class... Ls>
+struct Format {
+    static constexpr FmtParams make() {
+        FmtParams p{};
+        LevelDesc lv[] = {Ls::desc()...};
+        make_fmt_params(lv, (int)sizeof...(Ls), &p);
+        return p;
+    }
+    static constexpr FmtParams P = make();
+    static_assert(P.J > 0, "format cannot be composed");
+    using F = StatF<P.J, P.kind, P.bot, P.s, P.b, P.b0[0], P.b0[1], P.b0[2], P.ldim[0], P.ldim[1], P.ldim[2], P.jpop>;
+};
+
+// ---------------------------------------------------------------------------
+// Ray input and hit record
+// ---------------------------------------------------------------------------
+struct RayIn {
+    float o[3];
+    float tmin;
+    float d[3];
+    float tmax;
+};
+
+struct HitRec {
+    float t;
+    uint32_t rgba;
+    int x, y, z;
+    int face;
+    uint32_t status;
+};
+
+__device__ __forceinline__ HitRec miss_rec(uint32_t st) {
+    HitRec h;
+    h.t = __int_as_float(0x7f800000);
+    h.rgba = 0;
+    h.x = h.y = h.z = 0xFFFF;
+    h.face = 0;
+    h.status = st;
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 decisions (rare; kept out of line).  Each expression is the one the
+// FP64 reference stepper evaluates, one IEEE rounding per operation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double t64(float o, float d, int plane) {
+    return __ddiv_rn(__dsub_rn((double)plane, (double)o), (double)d);
+}
+
+struct Root64 {
+    double te, tx;
+    int e;
+};
+
+// Root slab test in FP64.  Axes with d == 0 were checked by the caller.
+static __device__ __noinline__ Root64 root64(RayIn r, int l0, int l1, int l2) {
+    const int ld[3] = {l0, l1, l2};
+    double best = -__longlong_as_double(0x7ff0000000000000ll);
+    double tx = (double)r.tmax;
+    int e = -1;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        if (r.d[i] == 0.0f) continue;
+        const int n = 1 << ld[i];
+        const int lo = r.d[i] > 0.0f ? 0 : n;
+        const int hi = r.d[i] > 0.0f ? n : 0;
+        const double a = t64(r.o[i], r.d[i], lo);
+        const double b = t64(r.o[i], r.d[i], hi);
+        if (a > best) { best = a; e = i; }
+        if (b < tx) tx = b;
+    }
+    Root64 R;
+    if (e >= 0 && best > (double)r.tmin) { R.te = best; R.e = e; }
+    else { R.te = (double)r.tmin; R.e = -1; }
+    R.tx = tx;
+    return R;
+}
+
+// Start voxel coordinate on a non-entry axis from the FP64 entry point.
+static __device__ __noinline__ int start_coord64(float o, float d, double te) {
+    const double p = __dadd_rn((double)o, __dmul_rn(te, (double)d));
+    double f = floor(p);
+    f = fmin(fmax(f, -2.0), 65536.0);
+    int v = (int)f;
+    if (p == f && d < 0.0f) v -= 1;
+    return v;
+}
+
+// Which of the crossing candidates comes first in FP64 (lowest axis on ties).
+static __device__ __noinline__ int argmin64(RayIn r, int p0, int p1, int p2) {
+    const int pl[3] = {p0, p1, p2};
+    int a = -1;
+    double m = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        if (r.d[i] == 0.0f) continue;
+        const double t = t64(r.o[i], r.d[i], pl[i]);
+        if (a < 0 || t < m) { m = t; a = i; }
+    }
+    return a;
+}
+
+// Is the crossing of `plane` on axis a at or after the exit?
+static __device__ __noinline__ bool exits64(RayIn r, int a, int plane, int l0, int l1, int l2) {
+    const Root64 R = root64(r, l0, l1, l2);
+    return !(t64(r.o[a], r.d[a], plane) < R.tx);
+}
+
+// Has the ray crossed plane B on axis a before the crossing of plane lp on
+// axis la that brought it into the current cell?
+static __device__ __noinline__ bool crossed64(RayIn r, int a, int B, int la, int lp) {
+    const double tb = t64(r.o[a], r.d[a], B);
+    const double tc = t64(r.o[la], r.d[la], lp);
+    return tb < tc || (tb == tc && a < la);
+}
+
+__device__ __forceinline__ bool near32(float x, float y) {
+    return !(fabsf(x - y) > kGuard * fmaxf(fabsf(x), fabsf(y)));
+}
+
+__device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint32_t i) { return __ldg(pool + i); }
+
+// ---------------------------------------------------------------------------
+// The traversal
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r) {
+    // Invalid rays: any NaN, or an infinite tmin.
+    if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
+        isnan(r.tmin) || isnan(r.tmax) || isinf(r.tmin))
+        return miss_rec(ST_INVALID);
+
+    int sg[3];
+    float inv[3], nf[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        sg[i] = r.d[i] > 0.0f ? 1 : (r.d[i] < 0.0f ? -1 : 0);
+        inv[i] = __frcp_rn(r.d[i]);
+        nf[i] = (float)(1 << f.ldim(i));
+    }
+
+    // ---- root slab test (FP32, FP64 when undecided) ----
+    float t0[3], best = -__int_as_float(0x7f800000), tx = r.tmax;
+    int e = -1;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        t0[i] = 0.0f;
+        if (sg[i] == 0) {
+            if (!(r.o[i] >= 0.0f && r.o[i] < nf[i])) return miss_rec(ST_MISS);
+            continue;
+        }
+        const float lo = sg[i] > 0 ? 0.0f : nf[i];
+        const float hi = sg[i] > 0 ? nf[i] : 0.0f;
+        t0[i] = (lo - r.o[i]) * inv[i];
+        const float t1 = (hi - r.o[i]) * inv[i];
+        if (t0[i] > best) { best = t0[i]; e = i; }
+        tx = fminf(tx, t1);
+    }
+    bool unsure = false;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+        if (sg[i] != 0 && i != e && near32(t0[i], best)) unsure = true;
+    if (e >= 0 && near32(best, r.tmin)) unsure = true;
+    int ea;
+    float te;
+    if (e >= 0 && best > r.tmin) { te = best; ea = e; }
+    else { te = r.tmin; ea = -1; }
+    bool miss;
+    if (unsure || near32(te, tx)) {
+        const Root64 R = root64(r, f.ldim(0), f.ldim(1), f.ldim(2));
+        ea = R.e;
+        te = (float)R.te;
+        tx = (float)R.tx;
+        miss = !(R.te < R.tx);
+    } else {
+        miss = !(te < tx);
+    }
+    if (miss) return miss_rec(ST_MISS);
+
+    // ---- start voxel ----
+    int v0[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int n = 1 << f.ldim(i);
+        int v;
+        if (i == ea) {
+            v = sg[i] > 0 ? 0 : n - 1;
+        } else {
+            const float p = fmaf(te, r.d[i], r.o[i]);
+            const float fl = floorf(p);
+            v = (int)fminf(fmaxf(fl, -2.0f), 65536.0f);
+            if (sg[i] != 0) {
+                const float rq = rintf(p);
+                if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
+                    const double te64 = ea >= 0 ? t64(r.o[ea], r.d[ea], sg[ea] > 0 ? 0 : (1 << f.ldim(ea)))
+                                                : (double)r.tmin;
+                    v = start_coord64(r.o[i], r.d[i], te64);
+                }
+            }
+        }
+        v0[i] = min(max(v, 0), n - 1);
+    }
+
+    // ---- root node ----
+    const uint32_t root = ldw(pool, 0);
+    if (root == 0) return miss_rec(ST_MISS);
+    uint32_t P[F::kMaxJ], M[F::kMaxJ];
+    {
+        const int k0 = f.kind(0);
+        if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
+        else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; }
+        else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; }
+    }
+    int j = 0;
+    int c[3];
+    {
+        const int s0 = f.s(0);
+#pragma unroll
+        for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
+    }
+    int la = ea;                                          // axis of the last crossing
+    int lp = ea >= 0 ? (sg[ea] > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
+    float tcur = te;
+    bool fresh = true;                                    // no step taken yet
+    const int J = f.J();
+
+    for (int it = 0; it < kIterCap; ++it) {
+        const int kind = f.kind(j);
+        const int s = f.s(j);
+        int bx, by, bz;
+        if (j == 0) { bx = f.b0(0); by = f.b0(1); bz = f.b0(2); }
+        else { bx = by = bz = f.b(j); }
+        const uint32_t lx = (uint32_t)c[0] & ((1u << bx) - 1u);
+        const uint32_t ly = (uint32_t)c[1] & ((1u << by) - 1u);
+        const uint32_t lz = (uint32_t)c[2] & ((1u << bz) - 1u);
+        uint32_t w = 0, idx;
+        bool occ;
+        if (kind == K_RAW) {
+            idx = lx | (ly << bx) | (lz << (bx + by));
+            w = ldw(pool, P[j] + idx);
+            occ = w != 0u;
+        } else {
+            idx = lx | (ly << 1) | (lz << 2);
+            occ = (M[j] >> idx) & 1u;
+        }
+        if (occ) {
+            // ---- descend (or hit at the last node level) ----
+            uint32_t term = w, Pn = 0, Mn = 0;
+            bool node_ready = false;
+            if (kind != K_RAW) {
+                const uint32_t rank = __popc(M[j] & ((1u << idx) - 1u));
+                if (f.has_svo() && kind == K_SVO) {
+                    const uint32_t addr = P[j] + 2u * rank;
+                    if (f.bot(j)) term = ldw(pool, addr);
+                    else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; }
+                } else {
+                    const uint32_t cp = ldw(pool, P[j] + 1u + rank);
+                    if (f.bot(j)) term = ldw(pool, cp);
+                    else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
+                }
+            }
+            if (j == J - 1) {
+                HitRec h;
+                h.t = tcur;
+                h.rgba = term;
+                h.x = c[0]; h.y = c[1]; h.z = c[2];
+                h.face = la >= 0 ? 1 + 2 * la + (sg[la] < 0 ? 1 : 0) : 0;
+                h.status = ST_HIT;
+                return h;
+            }
+            if (!node_ready) {
+                const int nk = f.kind(j + 1);
+                if (nk == K_RAW) { Pn = term; }
+                else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; }
+                else { Pn = term; Mn = ldw(pool, term) & 0xFFu; }
+            }
+            ++j;
+            P[j] = Pn;
+            M[j] = Mn;
+            const int sn = f.s(j), bn = f.b(j);
+            const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                if (fresh) { c[i] = v0[i] >> sn; continue; }
+                const int base = c[i] << bn;
+                const int topc = base + (1 << bn) - 1;
+                if (i == la) { c[i] = sg[i] > 0 ? base : topc; continue; }
+                if (sg[i] == 0) { c[i] = v0[i] >> sn; continue; }
+                const float p = fmaf(tcur, r.d[i], r.o[i]);
+                const float q = p * scale;
+                int cn = (int)fminf(fmaxf(floorf(q), (float)base), (float)topc);
+                const float rq = rintf(q);
+                if (rq > (float)base && rq <= (float)topc &&
+                    fabsf(q - rq) <= kGuard * (fabsf(tcur * r.d[i]) + fabsf(p)) * scale) {
+                    const int B = (int)rq;
+                    const bool cr = crossed64(r, i, B << sn, la, lp);
+                    cn = sg[i] > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
+                }
+                const int vs = v0[i] >> sn;
+                c[i] = sg[i] > 0 ? max(cn, vs) : min(cn, vs);
+            }
+            continue;
+        }
+
+        // ---- one Amanatides-Woo step at node level j ----
+        int pl[3];
+        float tn[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << s;
+            tn[i] = sg[i] != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
+        }
+        int a = 0;
+        float tm = tn[0];
+        if (tn[1] < tm) { a = 1; tm = tn[1]; }
+        if (tn[2] < tm) { a = 2; tm = tn[2]; }
+        if (!(tm < __int_as_float(0x7f800000))) {
+            if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) return miss_rec(ST_MISS);
+        }
+        bool und = false;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            if (sg[i] != 0 && i != a && near32(tm, tn[i])) und = true;
+        if (und) {
+            a = argmin64(r, pl[0], pl[1], pl[2]);
+            tm = tn[a];
+        }
+        bool out;
+        if (near32(tm, tx)) out = exits64(r, a, pl[a], f.ldim(0), f.ldim(1), f.ldim(2));
+        else out = !(tm < tx);
+        if (out) return miss_rec(ST_MISS);
+        const int old = c[a];
+        c[a] += sg[a];
+        tcur = tm;
+        la = a;
+        lp = pl[a];
+        fresh = false;
+        const int h = 31 - __clz((uint32_t)(old ^ c[a])) + s;  // highest changed voxel-coordinate bit
+        const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
+        if (h >= span) {
+            if (h >= f.ldim(a)) return miss_rec(ST_MISS);
+            const int jp = f.jpop(h);
+            const int sh = f.s(jp) - s;
+#pragma unroll
+            for (int i = 0; i < 3; i++) c[i] >>= sh;
+            j = jp;
+        }
+    }
+    return miss_rec(ST_ERROR);
+}
+
+// ---------------------------------------------------------------------------
+// Hit stores
+// ---------------------------------------------------------------------------
+template <int LAYOUT, class F>
+__device__ __forceinline__ void store_hit(const F& f, void* hits, uint64_t i, const HitRec& h) {
+    if (LAYOUT == 0) {
+        uint4 v;
+        v.x = __float_as_uint(h.t);
+        v.y = h.rgba;
+        v.z = ((uint32_t)h.x & 0xFFFFu) | ((uint32_t)h.y << 16);
+        v.w = ((uint32_t)h.z & 0xFFFFu) | ((uint32_t)h.face << 16) | (h.status << 24);
+        __stcs(reinterpret_cast<uint4*>(hits) + i, v);
+    } else {
+        uint2 v;
+        v.x = h.status == ST_HIT
+                  ? (uint32_t)h.x + ((uint32_t)h.y << f.ldim(0)) + ((uint32_t)h.z << (f.ldim(0) + f.ldim(1)))
+                  : 0xFFFFFFFFu;
+        v.y = __float_as_uint(h.t);
+        __stcs(reinterpret_cast<uint2*>(hits) + i, v);
+    }
+}
+
+__device__ __forceinline__ RayIn load_ray(const float4* __restrict__ rays, uint64_t i) {
+    const float4 a = __ldcs(rays + 2 * i);
+    const float4 b = __ldcs(rays + 2 * i + 1);
+    RayIn r;
+    r.o[0] = a.x; r.o[1] = a.y; r.o[2] = a.z; r.tmin = a.w;
+    r.d[0] = b.x; r.d[1] = b.y; r.d[2] = b.z; r.tmax = b.w;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Pinhole camera (FP32), pixel (px, py) through its centre.
+// ---------------------------------------------------------------------------
+struct CamDev {
+    float eye[3], f[3], r[3], u[3];
+    float tha, th;
+    uint32_t W, H;
+};
+
+__device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint32_t py) {
+    const float sx = (2.0f * ((float)px + 0.5f) / (float)c.W - 1.0f) * c.tha;
+    const float sy = (1.0f - 2.0f * ((float)py + 0.5f) / (float)c.H) * c.th;
+    float d[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) d[i] = c.f[i] + sx * c.r[i] + sy * c.u[i];
+    const float inv = 1.0f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    RayIn r;
+#pragma unroll
+    for (int i = 0; i < 3; i++) { r.o[i] = c.eye[i]; r.d[i] = d[i] * inv; }
+    r.tmin = 0.0f;
+    r.tmax = __int_as_float(0x7f800000);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <class F, int LAYOUT>
+__global__ void __launch_bounds__(256) k_trace(F f, const uint32_t* __restrict__ pool, const float4* __restrict__ rays,
+                                               uint64_t n, void* __restrict__ hits) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const RayIn r = load_ray(rays, i);
+    const HitRec h = trace_ray(f, pool, r);
+    store_hit<LAYOUT>(f, hits, i, h);
+}
+
+// Pixels i0 .. i0 + n - 1 (index px + W py); hit k of the launch is pixel i0 + k.
+template <class F, int LAYOUT>
+__global__ void __launch_bounds__(256) k_render(F f, const uint32_t* __restrict__ pool, CamDev cam, uint64_t i0,
+                                                uint64_t n, void* __restrict__ hits) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint64_t i = i0 + k;
+    const RayIn r = pinhole_ray(cam, (uint32_t)(i % cam.W), (uint32_t)(i / cam.W));
+    const HitRec h = trace_ray(f, pool, r);
+    store_hit<LAYOUT>(f, hits, k, h);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers, one set per format
+// ---------------------------------------------------------------------------
+struct KernelSet {
+    const char* spec;
+    bool specialized;
+    FmtParams params;
+    int (*trace)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits, int layout,
+                 int block, cudaStream_t st);
+    int (*render)(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
+                  int layout, int block, cudaStream_t st);
+};
+
+template <class F>
+struct Launch {
+    static F make(const FmtParams& p);
+    static int trace(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits, int layout,
+                     int block, cudaStream_t st) {
+        if (n == 0) return 0;
+        const F f = make(p);
+        const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
+        if (layout == 0) k_trace<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
+        else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
+        return (int)cudaGetLastError();
+    }
+    static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,
+                      void* hits, int layout, int block, cudaStream_t st) {
+        if (n == 0) return 0;
+        const F f = make(p);
+        const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
+        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
+        else k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
+        return (int)cudaGetLastError();
+    }
+};
+
+template <>
+inline DynF Launch<DynF>::make(const FmtParams& p) {
+    DynF f;
+    f.p = p;
+    return f;
+}
+template <class F>
+inline F Launch<F>::make(const FmtParams&) {
+    return F{};
+}
+
+template <class Fm>
+KernelSet make_kernel_set(const char* spec) {
+    using F = typename Fm::F;
+    return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render};
+}
+
+void register_kernel_set(const KernelSet* ks);
+
+struct KernelSetRegistrar {
+    explicit KernelSetRegistrar(const KernelSet* ks) { register_kernel_set(ks); }
+};
+
+}  // namespace vx

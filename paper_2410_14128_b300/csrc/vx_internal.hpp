@@ -1,0 +1,124 @@
+// vx_internal.hpp -- host-side declarations shared by the library's
+// translation units (not part of the public C ABI).
+#pragma once
+#include <stdint.h>
+
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/vx.h"
+#include "fmt.hpp"
+
+namespace vx {
+
+// ---------------------------------------------------------------------------
+// Errors: thread-local message returned by vx_last_error().
+// ---------------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+// ---------------------------------------------------------------------------
+// Format signatures (Table 1 grammar, log2 extents).
+// ---------------------------------------------------------------------------
+struct Level {
+    int kind;  // Kind
+    int e[3];  // Raw: W,H,D; SVO/SVDAG: L,L,L
+};
+
+struct Spec {
+    std::vector<Level> lv;
+    int ldim[3] = {0, 0, 0};
+    FmtParams fmt{};
+    std::string canonical;  // normalised text, e.g. "R(4,4,4) S(2) G(3)"
+};
+
+// Parses and validates a signature.  Returns VX_OK or a VX_E* code.
+int parse_spec(const char* text, Spec* out);
+
+// Morton order (x lowest bit, Fig. 5); extents may differ per axis: bits are
+// interleaved x, y, z while each axis still has bits left.
+void morton_decode(uint64_t m, const int e[3], uint32_t c[3]);
+uint64_t morton_encode(const uint32_t c[3], const int e[3]);
+
+// ---------------------------------------------------------------------------
+// Voxel sources (the voxelizer role of Sec. 4.1).
+// ---------------------------------------------------------------------------
+class VoxelSource {
+  public:
+    virtual ~VoxelSource() {}
+    // True only if the cube of side 2^log2s at (x0,y0,z0) holds no occupied voxel.
+    virtual bool empty(int64_t x0, int64_t y0, int64_t z0, int log2s) = 0;
+    // Words of the cube (side 2^log2s, corner a multiple of the side), x fastest.
+    virtual int block(int64_t x0, int64_t y0, int64_t z0, int log2s, uint32_t* out) = 0;
+};
+
+VoxelSource* make_dense_source(const uint32_t* words, const int ldim[3]);
+VoxelSource* make_brick_source(const vx_grid* g);
+
+// ---------------------------------------------------------------------------
+// Canonical build (paper layout) and its statistics.
+// ---------------------------------------------------------------------------
+struct BuildResult {
+    std::vector<uint32_t> words;  // word 0 = root pointer
+    uint64_t level_words[VX_MAX_LEVELS] = {};
+    uint64_t level_nodes[VX_MAX_LEVELS] = {};
+    uint64_t occupied = 0;
+};
+
+int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out);
+
+// Decodes the cube (side 2^log2s at x0,y0,z0) from a canonical buffer.
+int decode_cube(const Spec& spec, const uint32_t* words, uint64_t nwords, int64_t x0, int64_t y0, int64_t z0,
+                int log2s, uint32_t* out);
+
+// ---------------------------------------------------------------------------
+// Device side
+// ---------------------------------------------------------------------------
+struct CameraParams {
+    float eye[3];
+    float f[3], r[3], u[3];
+    float tha, th;  // tan(vfov/2) * W/H, tan(vfov/2)
+    uint32_t W, H;
+};
+
+struct KernelSet;  // kernels for one format (trace.cuh)
+
+// Device buffers and streams of the *_host calls (chunked copy/trace pipeline).
+struct Staging {
+    static constexpr uint64_t kChunk = 1u << 20;  // rays per chunk
+    void* d_rays[2] = {nullptr, nullptr};
+    void* d_hits[2] = {nullptr, nullptr};
+    void* streams[2] = {nullptr, nullptr};
+    void* ready = nullptr;
+};
+
+struct Volume {
+    Spec spec;
+    BuildResult built;
+    vx_stats stats{};
+    int device = -1;
+    uint32_t* d_pool = nullptr;
+    uint64_t pool_words = 0;
+    const KernelSet* kernels = nullptr;
+    std::mutex staging_mu;
+    Staging staging;
+};
+
+const KernelSet* kernels_for(const Spec& sp);
+bool kernel_set_specialized(const KernelSet* k);
+
+// Kernel registry: compile-time-composed kernels for known signatures, and
+// the run-time-described kernels for any other signature.
+const KernelSet* find_kernels(const std::string& canonical_spec);
+const KernelSet* generic_kernels();
+
+int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
+                 void* stream);
+int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
+                  const vx_trace_opts* o, void* stream);
+int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
+int camera_params(const vx_camera* cam, CameraParams* out);
+
+}  // namespace vx

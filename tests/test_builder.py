@@ -1,0 +1,188 @@
+"""Host-side tests of the product library (no GPU): the C ABI exports, the
+format parser, and the Morton-order builder checked against the oracle's
+independent decoder of the paper's layout and against hand-derived buffers."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2410_14128_b300 as vx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def build(spec, grid, **kw):
+    return vx.Volume(spec, grid, upload=False, **kw)
+
+
+# ---------------------------------------------------------------------------
+# ABI
+# ---------------------------------------------------------------------------
+def header_functions():
+    with open(os.path.join(ROOT, "include", "vx.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(vx_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_library_exports_every_header_function():
+    import ctypes
+    names = header_functions()
+    assert len(names) >= 12
+    L = ctypes.CDLL(vx.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(vx.exported_symbols())
+    assert vx.lib().vx_version() >= 10000
+
+
+# ---------------------------------------------------------------------------
+# Spec parser
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec,code", [
+    ("", vx.VX_EINVAL), ("Q(3)", vx.VX_EINVAL), ("R(1,1)", vx.VX_EINVAL), ("S(0)", vx.VX_EINVAL),
+    ("R(2,2,2) R(1,2,1)", vx.VX_EINVAL),            # lower levels must be cubic (Sec. 5)
+    ("R(2,2,2) S(1)", vx.VX_EINVAL),                # 8^3 spec on a 16^3 grid
+    ("D(2,2,2,4) R(2,2,2)", vx.VX_EUNSUPPORTED),    # distance-field levels are not built yet
+])
+def test_bad_specs_rejected(spec, code):
+    g = np.zeros((16, 16, 16), np.uint32)
+    with pytest.raises(vx.VxError) as e:
+        build(spec, g)
+    assert e.value.code == code
+
+
+def test_n_cubed_shorthand_matches_explicit():
+    g = synth.random_grid(3, (16, 16, 16), 0.1)
+    a = build("R(2^3) G(2)", g).canonical()
+    b = build("R(2, 2, 2) G(2)", g).canonical()
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# Canonical buffer: bit-exact against hand-derived examples of the layout
+# ---------------------------------------------------------------------------
+def _layout():
+    with open(os.path.join(GOLDEN, "layout_examples.json")) as f:
+        return json.load(f)["examples"]
+
+
+@pytest.mark.parametrize("ex", _layout(), ids=lambda e: e["name"])
+def test_builder_reproduces_hand_built_buffers(ex):
+    nx, ny, nz = ex["dims"]
+    g = np.zeros((nz, ny, nx), np.uint32)
+    for x, y, z, c in ex["voxels"]:
+        g[z, y, x] = c
+    words = build(ex["spec"], g).canonical()
+    exp = np.zeros(ex["nwords"], np.uint32)
+    for k, v in ex["set"].items():
+        exp[int(k)] = v
+    assert words.tolist() == exp.tolist()
+
+
+# ---------------------------------------------------------------------------
+# decode(build(G)) == G for many formats, by the oracle's decoder
+# ---------------------------------------------------------------------------
+SPECS_16 = ["R(4,4,4)", "S(4)", "G(4)", "R(2,2,2) R(2,2,2)", "R(1,1,1) S(1) G(2)", "S(2) R(2,2,2)",
+            "G(2) S(2)", "R(3,3,3) G(1)", "S(1) S(1) S(1) S(1)", "R(2,2,2) S(1) G(1)", "G(1) R(3,3,3)"]
+
+
+@pytest.mark.parametrize("spec", SPECS_16)
+@pytest.mark.parametrize("p", [0.0, 0.03, 0.3, 1.0])
+def test_decode_roundtrip_oracle(spec, p):
+    g = synth.random_grid(hash((spec, p)) & 0xFFFF, (16, 16, 16), p, colors=3)
+    v = build(spec, g)
+    words = v.canonical()
+    assert np.array_equal(oracle.decode(words, spec), g)
+    assert np.array_equal(v.decode_brick(0, 0, 0, 4), g)
+    assert np.array_equal(v.decode_brick(8, 0, 8, 3), g[8:16, 0:8, 8:16])
+    assert v.stats()["occupied_voxels"] == int((g != 0).sum())
+
+
+@pytest.mark.parametrize("spec", ["R(1,0,2) R(2,2,2)", "R(3,1,2) S(2)", "R(0,2,1) G(2)"])
+def test_non_cubic_top_level(spec):
+    (lx, ly, lz), _ = oracle.spec_dims(spec)
+    g = synth.random_grid(9, (1 << lz, 1 << ly, 1 << lx), 0.2)
+    words = build(spec, g).canonical()
+    assert np.array_equal(oracle.decode(words, spec), g)
+
+
+def test_terrain_roundtrip_64():
+    g = synth.terrain_volume(5, 64)
+    for spec in ["R(2,2,2) S(2) G(2)", "R(2,2,2) R(2,2,2) R(2,2,2)", "S(4) R(2,2,2)", "G(6)"]:
+        assert np.array_equal(oracle.decode(build(spec, g).canonical(), spec), g), spec
+
+
+def test_brick_callback_matches_dense():
+    g = synth.random_grid(21, (32, 32, 32), 0.05)
+
+    def fill(user, x0, y0, z0, l2, out):
+        s = 1 << l2
+        blk = np.ascontiguousarray(g[z0:z0 + s, y0:y0 + s, x0:x0 + s]).reshape(-1)
+        np.ctypeslib.as_array(out, shape=(s * s * s,))[:] = blk
+        return 0
+
+    for spec in ["R(2,2,2) G(3)", "S(3) R(2,2,2)"]:
+        a = build(spec, g).canonical()
+        b = vx.Volume(spec, log2_dim=(5, 5, 5), fill_brick=fill, upload=False).canonical()
+        assert np.array_equal(a, b), spec
+
+
+# ---------------------------------------------------------------------------
+# Invariants and closed forms
+# ---------------------------------------------------------------------------
+def test_empty_volume_is_one_word():
+    g = np.zeros((16, 16, 16), np.uint32)
+    for spec in SPECS_16:
+        w = build(spec, g).canonical()
+        assert w.tolist() == [0], spec
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+def test_full_grid_closed_forms(L):
+    n = 1 << L
+    g = np.full((n, n, n), 0xFF00FF00, np.uint32)
+    s = build(f"S({L})", g).stats()
+    nodes = sum(8 ** d for d in range(L + 1))  # every node of a complete octree, leaves included
+    assert s["level_nodes"][0] == nodes
+    assert s["canonical_words"] == 1 + 2 * nodes
+    d = build(f"G({L})", g).stats()
+    # one distinct node per depth: L internal nodes (8 pointers each) and one leaf word
+    assert d["level_nodes"][0] == L + 1
+    assert d["canonical_words"] == 1 + 1 + 9 * L
+    r = build(f"R({L},{L},{L})", g).stats()
+    assert r["canonical_words"] == 1 + n ** 3
+
+
+@pytest.mark.parametrize("seed,p", [(1, 0.02), (2, 0.2), (3, 0.6)])
+def test_svdag_never_larger_than_svo(seed, p):
+    g = synth.random_grid(seed, (32, 32, 32), p, colors=2)
+    for top in ["", "R(1,1,1) ", "R(2,2,2) "]:
+        L = 5 - (0 if not top else int(top[2]))
+        so = build(f"{top}S({L})", g).stats()
+        dg = build(f"{top}G({L})", g).stats()
+        k = 0 if not top else 1
+        assert dg["level_nodes"][k] <= so["level_nodes"][k]
+
+
+@pytest.mark.parametrize("spec", ["R(2,2,2) G(3)", "R(3,3,3) G(2)", "S(2) G(3)"])
+def test_whole_level_dedup_never_larger(spec):
+    g = synth.terrain_volume(8, 32)
+    whole = build(spec, g, dedup=vx.DEDUP_WHOLE_LEVEL)
+    per = build(spec, g, dedup=vx.DEDUP_PER_SUBVOLUME)
+    assert whole.stats()["canonical_words"] <= per.stats()["canonical_words"]
+    assert np.array_equal(oracle.decode(per.canonical(), spec), g)
+    assert np.array_equal(oracle.decode(whole.canonical(), spec), g)
+
+
+def test_single_colour_dedups_strongly():
+    # a single-coloured volume shares sub-volume interiors across the level
+    g = synth.random_grid(4, (32, 32, 32), 0.5, colors=1)
+    g[:, :16, :] = np.uint32(0xFF0000FF)
+    whole = build("R(2,2,2) G(3)", g, dedup=vx.DEDUP_WHOLE_LEVEL).stats()["canonical_words"]
+    per = build("R(2,2,2) G(3)", g, dedup=vx.DEDUP_PER_SUBVOLUME).stats()["canonical_words"]
+    assert whole < per
