@@ -185,7 +185,8 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
 
 /* Trace options (NULL = defaults / autotuned values).
  *   mode   VX_MODE_*;
- *   block  threads per block (multiple of 32, <= 1024), 0 = default;
+ *   block  threads per block: 0 = default, else a multiple of 32 in
+ *          [32, 256] (VX_EINVAL otherwise);
  *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = default;
  *   smem_top  1 = stage the top Raw level in shared memory when it fits,
  *          0 = read it from global memory, -1 = default. */
@@ -208,6 +209,16 @@ typedef struct vx_trace_opts {
  * on a grid of 2^32 voxels or more), VX_ECUDA (launch failure). */
 int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
              const vx_trace_opts* opts, void* stream);
+
+/* Same results as vx_trace from an instrumented kernel that also adds, over
+ * all rays, into the device array counters[0..2] (caller-zeroed, 8-byte
+ * aligned, unsigned 64-bit): [0] bytes of the format read by the traversal
+ * (Raw cell 4, octree node 8, DAG mask 4 + pointer 4, leaf terminating
+ * integer 4), [1] loop iterations, [2] decisions re-taken in FP64.  For
+ * measurement: the bytes a ray must read from the format are the
+ * algorithmic traffic of the method. */
+int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
+                     const vx_trace_opts* opts, void* stream, unsigned long long* counters);
 
 /* Same as vx_trace with host arrays: the rays are copied to the device in
  * chunks, traced and the hits copied back, copies overlapped with tracing.

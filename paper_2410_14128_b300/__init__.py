@@ -81,6 +81,8 @@ _SIGS = {
                                        ctypes.c_uint32, ctypes.c_void_p]),
     "vx_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_trace_counted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                      ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_raygen_pinhole": (ctypes.c_int, [ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_void_p]),
@@ -251,6 +253,16 @@ class Volume:
         o = _opts(**opts)
         _check(lib().vx_trace(self._h, ctypes.c_void_p(rays.data_ptr()), n, ctypes.c_void_p(hits.data_ptr()),
                               layout, ctypes.byref(o), _stream_handle(stream)))
+        return hits
+
+    def trace_counted(self, rays, hits, counters, layout: int = HIT_FULL, stream=None, **opts):
+        """As trace(), adding [bytes read, iterations, FP64 decisions] into
+        `counters` (CUDA int64 tensor of 3, caller-zeroed)."""
+        n = rays.shape[0]
+        o = _opts(**opts)
+        _check(lib().vx_trace_counted(self._h, ctypes.c_void_p(rays.data_ptr()), n, ctypes.c_void_p(hits.data_ptr()),
+                                      layout, ctypes.byref(o), _stream_handle(stream),
+                                      ctypes.c_void_p(counters.data_ptr())))
         return hits
 
     def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,

@@ -54,6 +54,18 @@ int check_trace_args(vx_volume v, const void* rays, uint64_t n, const void* hits
     if (layout == VX_HIT_COMPACT && v->v.spec.ldim[0] + v->v.spec.ldim[1] + v->v.spec.ldim[2] >= 32)
         return fail(VX_EINVAL, "compact hits need fewer than 2^32 voxels");
     if (n == 0) return VX_OK;
+    return VX_OK;
+}
+
+int check_opts(const vx_trace_opts* o) {
+    if (!o) return VX_OK;
+    if (o->block != 0 && (o->block < 32 || o->block > 256 || (o->block & 31)))
+        return fail(VX_EINVAL, "block must be 0 or a multiple of 32 in [32, 256], got %d", o->block);
+    if (o->mode < VX_MODE_AUTO || o->mode > VX_MODE_PERSISTENT) return fail(VX_EINVAL, "bad mode %d", o->mode);
+    return VX_OK;
+}
+
+int check_ptrs(const void* rays, const void* hits, int32_t layout) {
     if (rays && !aligned(rays, 16)) return fail(VX_EINVAL, "rays must be 16-byte aligned");
     if (!hits) return fail(VX_EINVAL, "hits is NULL");
     if (!aligned(hits, layout == VX_HIT_FULL ? 16 : 8)) return fail(VX_EINVAL, "hits misaligned for the layout");
@@ -238,18 +250,36 @@ extern "C" int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits,
                         const vx_trace_opts* opts, void* stream) {
     clear_error();
     int rc = check_trace_args(v, rays, n, hits, hit_layout);
+    if (!rc) rc = check_opts(opts);
     if (rc || n == 0) return rc;
+    if ((rc = check_ptrs(rays, hits, hit_layout))) return rc;
     if (!rays) return fail(VX_EINVAL, "rays is NULL");
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
     return launch_trace(v->v, rays, n, hits, hit_layout, opts, stream);
 }
 
+extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
+                                const vx_trace_opts* opts, void* stream, unsigned long long* counters) {
+    clear_error();
+    int rc = check_trace_args(v, rays, n, hits, hit_layout);
+    if (!rc) rc = check_opts(opts);
+    if (rc || n == 0) return rc;
+    if ((rc = check_ptrs(rays, hits, hit_layout))) return rc;
+    if (!rays) return fail(VX_EINVAL, "rays is NULL");
+    if (!counters || !aligned(counters, 8)) return fail(VX_EINVAL, "counters must be an 8-byte aligned device array");
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return launch_trace_count(v->v, rays, n, hits, hit_layout, opts, stream, counters);
+}
+
 extern "C" int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,
                              const vx_trace_opts* opts, void* stream) {
     clear_error();
     int rc = check_trace_args(v, rays_host, n, hits_host, hit_layout);
+    if (!rc) rc = check_opts(opts);
     if (rc || n == 0) return rc;
+    if ((rc = check_ptrs(rays_host, hits_host, hit_layout))) return rc;
     if (!rays_host) return fail(VX_EINVAL, "rays is NULL");
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
@@ -284,6 +314,8 @@ extern "C" int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t 
     if (rc) return rc;
     const uint64_t n = (uint64_t)cp.W * cp.H;
     rc = check_trace_args(v, nullptr, n, hits, hit_layout);
+    if (!rc) rc = check_opts(opts);
+    if (!rc) rc = check_ptrs(nullptr, hits, hit_layout);
     if (rc) return rc;
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
@@ -298,6 +330,8 @@ extern "C" int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host
     if (rc) return rc;
     const uint64_t n = (uint64_t)cp.W * cp.H;
     rc = check_trace_args(v, nullptr, n, hits_host, hit_layout);
+    if (!rc) rc = check_opts(opts);
+    if (!rc) rc = check_ptrs(nullptr, hits_host, hit_layout);
     if (rc) return rc;
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");

@@ -16,7 +16,8 @@ std::vector<const KernelSet*>& registry() {
     static std::vector<const KernelSet*> r;
     return r;
 }
-const KernelSet g_generic = {"*", false, FmtParams{}, &Launch<DynF>::trace, &Launch<DynF>::render};
+const KernelSet g_generic = {"*", false, FmtParams{}, &Launch<DynF>::trace, &Launch<DynF>::render,
+                             &Launch<DynF>::trace_count};
 
 CamDev to_dev(const CameraParams& c) {
     CamDev d;
@@ -64,6 +65,15 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     const int block = pick_block(o);
     int e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout, block,
                              (cudaStream_t)stream);
+    if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return VX_OK;
+}
+
+int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout,
+                       const vx_trace_opts* o, void* stream, unsigned long long* counters) {
+    const int block = pick_block(o);
+    int e = v.kernels->trace_count(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout,
+                                   block, (cudaStream_t)stream, counters);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }

@@ -38,7 +38,6 @@
 namespace vx {
 
 constexpr float kGuard = 9.5367431640625e-07f;  // 2^-20
-constexpr int kIterCap = 1 << 22;
 
 enum : uint32_t { ST_MISS = 0, ST_HIT = 1, ST_INVALID = 2, ST_ERROR = 3 };
 
@@ -121,6 +120,12 @@ struct HitRec {
     int x, y, z;
     int face;
     uint32_t status;
+};
+
+// Per-ray work counters of the instrumented kernels: words of the format
+// read (in bytes), loop iterations, and decisions re-taken in FP64.
+struct Cnt {
+    uint32_t bytes = 0, iters = 0, fp64 = 0;
 };
 
 __device__ __forceinline__ HitRec miss_rec(uint32_t st) {
@@ -217,8 +222,12 @@ __device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint3
 // ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
-template <class F>
-__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r) {
+template <bool COUNT, class F>
+__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r, Cnt& cnt) {
+#define VX_CNT(field, v) \
+    do {                 \
+        if (COUNT) cnt.field += (v); \
+    } while (0)
     // Invalid rays: any NaN, or an infinite tmin.
     if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
         isnan(r.tmin) || isnan(r.tmax) || isinf(r.tmin))
@@ -261,6 +270,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
     else { te = r.tmin; ea = -1; }
     bool miss;
     if (unsure || near32(te, tx)) {
+        VX_CNT(fp64, 1);
         const Root64 R = root64(r, f.ldim(0), f.ldim(1), f.ldim(2));
         ea = R.e;
         te = (float)R.te;
@@ -286,6 +296,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             if (sg[i] != 0) {
                 const float rq = rintf(p);
                 if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
+                    VX_CNT(fp64, 1);
                     const double te64 = ea >= 0 ? t64(r.o[ea], r.d[ea], sg[ea] > 0 ? 0 : (1 << f.ldim(ea)))
                                                 : (double)r.tmin;
                     v = start_coord64(r.o[i], r.d[i], te64);
@@ -297,13 +308,14 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
 
     // ---- root node ----
     const uint32_t root = ldw(pool, 0);
+    VX_CNT(bytes, 4);
     if (root == 0) return miss_rec(ST_MISS);
     uint32_t P[F::kMaxJ], M[F::kMaxJ];
     {
         const int k0 = f.kind(0);
         if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
-        else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; }
-        else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; }
+        else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+        else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
     }
     int j = 0;
     int c[3];
@@ -317,8 +329,12 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
     float tcur = te;
     bool fresh = true;                                    // no step taken yet
     const int J = f.J();
+    // A ray crosses at most nx + ny + nz cells of any level and each step
+    // costs at most J descents; past this bound the ray reports ST_ERROR.
+    const int cap = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (J + 2);
 
-    for (int it = 0; it < kIterCap; ++it) {
+    for (int it = 0; it < cap; ++it) {
+        VX_CNT(iters, 1);
         const int kind = f.kind(j);
         const int s = f.s(j);
         int bx, by, bz;
@@ -332,6 +348,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         if (kind == K_RAW) {
             idx = lx | (ly << bx) | (lz << (bx + by));
             w = ldw(pool, P[j] + idx);
+            VX_CNT(bytes, 4);
             occ = w != 0u;
         } else {
             idx = lx | (ly << 1) | (lz << 2);
@@ -345,12 +362,13 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
                 const uint32_t rank = __popc(M[j] & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = P[j] + 2u * rank;
-                    if (f.bot(j)) term = ldw(pool, addr);
-                    else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; }
+                    if (f.bot(j)) { term = ldw(pool, addr); VX_CNT(bytes, 4); }
+                    else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
                     const uint32_t cp = ldw(pool, P[j] + 1u + rank);
                     if (f.bot(j)) term = ldw(pool, cp);
                     else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
+                    VX_CNT(bytes, 8);
                 }
             }
             if (j == J - 1) {
@@ -365,8 +383,8 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             if (!node_ready) {
                 const int nk = f.kind(j + 1);
                 if (nk == K_RAW) { Pn = term; }
-                else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; }
-                else { Pn = term; Mn = ldw(pool, term) & 0xFFu; }
+                else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
+                else { Pn = term; Mn = ldw(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
             P[j] = Pn;
@@ -386,6 +404,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
                 const float rq = rintf(q);
                 if (rq > (float)base && rq <= (float)topc &&
                     fabsf(q - rq) <= kGuard * (fabsf(tcur * r.d[i]) + fabsf(p)) * scale) {
+                    VX_CNT(fp64, 1);
                     const int B = (int)rq;
                     const bool cr = crossed64(r, i, B << sn, la, lp);
                     cn = sg[i] > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
@@ -416,11 +435,12 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         for (int i = 0; i < 3; i++)
             if (sg[i] != 0 && i != a && near32(tm, tn[i])) und = true;
         if (und) {
+            VX_CNT(fp64, 1);
             a = argmin64(r, pl[0], pl[1], pl[2]);
             tm = tn[a];
         }
         bool out;
-        if (near32(tm, tx)) out = exits64(r, a, pl[a], f.ldim(0), f.ldim(1), f.ldim(2));
+        if (near32(tm, tx)) { VX_CNT(fp64, 1); out = exits64(r, a, pl[a], f.ldim(0), f.ldim(1), f.ldim(2)); }
         else out = !(tm < tx);
         if (out) return miss_rec(ST_MISS);
         const int old = c[a];
@@ -441,6 +461,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         }
     }
     return miss_rec(ST_ERROR);
+#undef VX_CNT
 }
 
 // ---------------------------------------------------------------------------
@@ -507,8 +528,36 @@ __global__ void __launch_bounds__(256) k_trace(F f, const uint32_t* __restrict__
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const RayIn r = load_ray(rays, i);
-    const HitRec h = trace_ray(f, pool, r);
+    Cnt cnt;
+    const HitRec h = trace_ray<false>(f, pool, r, cnt);
     store_hit<LAYOUT>(f, hits, i, h);
+}
+
+// Instrumented twin of k_trace: same results, plus totals of the per-ray
+// counters in counters[0..2] (bytes of the format read, iterations, FP64
+// decisions), summed per warp then added atomically.
+template <class F, int LAYOUT>
+__global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __restrict__ pool,
+                                                     const float4* __restrict__ rays, uint64_t n,
+                                                     void* __restrict__ hits, unsigned long long* counters) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt cnt;
+    if (i < n) {
+        const RayIn r = load_ray(rays, i);
+        const HitRec h = trace_ray<true>(f, pool, r, cnt);
+        store_hit<LAYOUT>(f, hits, i, h);
+    }
+    unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64;
+    for (int o = 16; o > 0; o >>= 1) {
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        it += __shfl_down_sync(0xffffffffu, it, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counters + 0, b);
+        atomicAdd(counters + 1, it);
+        atomicAdd(counters + 2, d);
+    }
 }
 
 // Pixels i0 .. i0 + n - 1 (index px + W py); hit k of the launch is pixel i0 + k.
@@ -519,7 +568,8 @@ __global__ void __launch_bounds__(256) k_render(F f, const uint32_t* __restrict_
     if (k >= n) return;
     const uint64_t i = i0 + k;
     const RayIn r = pinhole_ray(cam, (uint32_t)(i % cam.W), (uint32_t)(i / cam.W));
-    const HitRec h = trace_ray(f, pool, r);
+    Cnt cnt;
+    const HitRec h = trace_ray<false>(f, pool, r, cnt);
     store_hit<LAYOUT>(f, hits, k, h);
 }
 
@@ -534,6 +584,8 @@ struct KernelSet {
                  int block, cudaStream_t st);
     int (*render)(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
+    int (*trace_count)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+                       int layout, int block, cudaStream_t st, unsigned long long* counters);
 };
 
 template <class F>
@@ -546,6 +598,15 @@ struct Launch {
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
         if (layout == 0) k_trace<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
         else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
+        return (int)cudaGetLastError();
+    }
+    static int trace_count(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+                           int layout, int block, cudaStream_t st, unsigned long long* counters) {
+        if (n == 0) return 0;
+        const F f = make(p);
+        const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
+        if (layout == 0) k_trace_count<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+        else k_trace_count<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -573,7 +634,7 @@ inline F Launch<F>::make(const FmtParams&) {
 template <class Fm>
 KernelSet make_kernel_set(const char* spec) {
     using F = typename Fm::F;
-    return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render};
+    return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render, &Launch<F>::trace_count};
 }
 
 void register_kernel_set(const KernelSet* ks);

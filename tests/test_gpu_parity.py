@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA traversal (through the C ABI) against the FP64 oracle,
+element by element, on seeded inputs with the shapes of the paper's
+workloads (noise volume, terrain) plus small adversarial grids."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2410_14128_b300 as vx
+from parity_util import compare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vx.lib()
+
+
+def gpu_trace(vol, rays, layout=vx.HIT_FULL, **opts):
+    r = torch.from_numpy(np.ascontiguousarray(rays, np.float32)).cuda()
+    h = vx.alloc_hits(len(rays), layout)
+    vol.trace(r, h, layout, **opts)
+    torch.cuda.synchronize()
+    return vx.hits_to_numpy(h, layout)
+
+
+def lattice_rays(seed, dims, count):
+    rng = np.random.default_rng(seed)
+    o = rng.integers(-8, 4 * max(dims) + 8, size=(count, 3)) / 4.0
+    d = rng.integers(-2, 3, size=(count, 3)).astype(np.float64)
+    d[np.all(d == 0, axis=1)] = (1, 1, 0)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = np.zeros((count, 8), np.float32)
+    r[:, 0:3], r[:, 4:7], r[:, 7] = o, d, np.inf
+    return r
+
+
+def ranged(rays, seed):
+    rng = np.random.default_rng(seed)
+    r = rays.copy()
+    sel = rng.random(len(r)) < 0.3
+    r[sel, 3] = rng.uniform(0, 6, sel.sum())
+    r[sel, 7] = r[sel, 3] + rng.uniform(0, 15, sel.sum())
+    return r
+
+
+# ---------------------------------------------------------------------------
+# 64^3 noise volume, 256x256 pinhole rays (both readings of the SVO -> Raw 4^3 format)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["S(4) R(2,2,2)", "S(3) R(3,3,3)"])
+@pytest.mark.parametrize("layout", [vx.HIT_FULL, vx.HIT_COMPACT])
+def test_noise64_pinhole(spec, layout):
+    g = synth.value_noise_volume(101, 64)
+    cam = synth.camera(102, 64, 256, 256, mode="sphere")
+    rays = oracle.pinhole(cam)
+    vol = vx.Volume(spec, g)
+    assert vol.stats()["specialized"]
+    h = gpu_trace(vol, rays, layout)
+    res = compare(g, rays, h, layout)
+    assert res["hits"] > 10000
+
+
+def test_noise64_incoherent_and_ranges():
+    g = synth.value_noise_volume(103, 64)
+    rays = ranged(synth.incoherent_rays(104, 64, 60000), 105)
+    for spec in ["S(4) R(2,2,2)", "S(3) R(3,3,3)"]:
+        vol = vx.Volume(spec, g)
+        compare(g, rays, gpu_trace(vol, rays))
+
+
+# ---------------------------------------------------------------------------
+# Small grids, adversarial rays, compile-time and run-time-described formats
+# ---------------------------------------------------------------------------
+SMALL_SPECS = ["R(4,4,4)", "S(4)", "G(4)", "R(2,2,2) R(2,2,2)", "R(1,1,1) S(1) G(2)", "S(2) R(2,2,2)",
+               "G(2) S(2)", "R(3,3,3) G(1)", "S(1) S(1) S(1) S(1)", "G(1) R(3,3,3)"]
+
+
+@pytest.mark.parametrize("spec", SMALL_SPECS)
+@pytest.mark.parametrize("p", [0.02, 0.25])
+def test_small_grids_adversarial(spec, p):
+    g = synth.random_grid(hash((spec, p)) & 0xFFFF, (16, 16, 16), p, colors=4)
+    dims = (16, 16, 16)
+    rays = np.concatenate([
+        ranged(synth.box_rays(7, 16, 6, 20000), 8),
+        ranged(synth.aimed_rays(9, dims, 20000), 10),
+        lattice_rays(11, dims, 20000),
+    ])
+    vol = vx.Volume(spec, g)
+    res = compare(g, rays, gpu_trace(vol, rays))
+    assert res["hits"] > 1000
+
+
+@pytest.mark.parametrize("spec", ["R(1,0,2) R(2,2,2)", "R(3,1,2) S(2)", "R(0,2,1) G(2)"])
+def test_non_cubic_top(spec):
+    (lx, ly, lz), _ = oracle.spec_dims(spec)
+    g = synth.random_grid(12, (1 << lz, 1 << ly, 1 << lx), 0.1)
+    dims = (1 << lx, 1 << ly, 1 << lz)
+    rays = np.concatenate([synth.aimed_rays(13, dims, 20000), lattice_rays(14, dims, 10000)])
+    compare(g, rays, gpu_trace(vx.Volume(spec, g), rays))
+
+
+def test_empty_and_full_volumes():
+    dims = (32, 32, 32)
+    rays = np.concatenate([synth.aimed_rays(15, dims, 10000), synth.box_rays(16, 32, 4, 10000)])
+    for fill in (0, 0xFF123456):
+        g = np.full((32, 32, 32), fill, np.uint32)
+        for spec in ["R(2,2,2) S(1) G(2)", "G(5)", "R(5,5,5)"]:
+            compare(g, rays, gpu_trace(vx.Volume(spec, g), rays))
+
+
+def test_degenerate_rays():
+    g = synth.random_grid(17, (16, 16, 16), 0.2)
+    nan, inf = np.nan, np.inf
+    rows = [
+        [nan, 1, 1, 0, 1, 0, 0, inf], [1, 1, 1, 0, 1, nan, 0, inf], [1, 1, 1, inf, 1, 0, 0, inf],
+        [1, 1, 1, 0, 1, 0, 0, nan], [1.5, 1.5, 1.5, 0, 0, 0, 0, inf], [8.0, 8.0, 8.0, 0, 0, 0, 0, 5.0],
+        [-1, 2.5, 2.5, 0, 1, -0.0, 0.0, inf], [-1, 2.5, 2.5, 3, 1, 0, 0, 2],
+        [4.0, 4.0, 4.0, 0, 0, 0, 1, inf], [16.0, 4, 4, 0, -1, 0, 0, inf], [0.0, 0.0, 0.0, 0, 1, 1, 1, inf],
+        [1e-30, 3.5, 3.5, 0, 1e-30, 1, 0, inf], [5, 5, -3, 0, 1e-38, 1e-38, 1, inf],
+    ]
+    rays = np.array(rows, np.float32)
+    for spec in ["R(2,2,2) S(2)", "G(4)"]:
+        compare(g, rays, gpu_trace(vx.Volume(spec, g), rays))
+
+
+def test_ragged_sizes_and_block_sizes():
+    g = synth.random_grid(18, (32, 32, 32), 0.1)
+    vol = vx.Volume("R(2,2,2) G(3)", g)
+    for n in (1, 31, 257, 4097):
+        rays = synth.aimed_rays(19 + n, (32, 32, 32), n)
+        compare(g, rays, gpu_trace(vol, rays))
+    rays = synth.aimed_rays(20, (32, 32, 32), 10000)
+    ref = gpu_trace(vol, rays)
+    for b in (32, 64, 128, 256):
+        assert np.array_equal(gpu_trace(vol, rays, block=b), ref)
+    for b in (16, 48, 512):
+        with pytest.raises(vx.VxError) as e:
+            gpu_trace(vol, rays, block=b)
+        assert e.value.code == vx.VX_EINVAL
+    # n = 0 is a no-op
+    vol.trace(torch.empty((0, 8), device="cuda"), vx.alloc_hits(0))
+
+
+# ---------------------------------------------------------------------------
+# Terrain: 128^3 full parity, 512^3 in the benchmark's configuration (sampled)
+# ---------------------------------------------------------------------------
+def test_terrain128_formats():
+    g = synth.terrain_volume(21, 128)
+    cam = synth.camera(22, 128, 320, 240, mode="above")
+    rays = np.concatenate([oracle.pinhole(cam), synth.incoherent_rays(23, 128, 50000)])
+    for spec in ["R(3,3,3) S(2) G(2)", "R(3,3,3) R(2,2,2) R(2,2,2)", "R(2,2,2) G(5)", "S(7)", "G(7)",
+                 "S(3) R(2,2,2) G(2)"]:
+        compare(g, rays, gpu_trace(vx.Volume(spec, g), rays))
+
+
+@pytest.fixture(scope="module")
+def terrain512():
+    return synth.terrain_volume(2024, 512)
+
+
+@pytest.mark.parametrize("spec", ["R(4,4,4) S(2) G(3)", "R(3,3,3) R(3,3,3) R(3,3,3)"])
+def test_terrain512_full_size_sampled(terrain512, spec):
+    g = terrain512
+    vol = vx.Volume(spec, g)
+    assert vol.stats()["specialized"]
+    cam = synth.camera(2025, 512, 1920, 1080, mode="above")
+    prim = oracle.pinhole(cam)
+    inc = synth.incoherent_rays(2026, 512, 1 << 21)
+    # full-size launches, as the benchmark runs them; the oracle checks a sample
+    hp = gpu_trace(vol, prim)
+    hi = gpu_trace(vol, inc)
+    rng = np.random.default_rng(7)
+    sp = rng.choice(len(prim), 150000, replace=False)
+    si = rng.choice(len(inc), 150000, replace=False)
+    compare(g, prim[sp], hp[sp])
+    compare(g, inc[si], hi[si])
+
+
+# ---------------------------------------------------------------------------
+# Ray generation and the fused / host entry points
+# ---------------------------------------------------------------------------
+def test_raygen_matches_oracle_pinhole():
+    for seed, (W, H) in [(31, (256, 256)), (32, (1920, 1080)), (33, (7, 5))]:
+        cam = synth.camera(seed, 512, W, H, mode="above")
+        ref = oracle.pinhole(cam)
+        got = vx.raygen_pinhole(cam).cpu().numpy()
+        assert np.array_equal(got[:, 0:4], ref[:, 0:4])
+        assert np.array_equal(got[:, 7], ref[:, 7])
+        np.testing.assert_allclose(got[:, 4:7], ref[:, 4:7], rtol=0, atol=6e-7)
+
+
+def test_render_equals_trace_of_raygen():
+    g = synth.terrain_volume(41, 128)
+    vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
+    cam = synth.camera(42, 128, 640, 360, mode="above")
+    rays = vx.raygen_pinhole(cam)
+    h1 = vx.alloc_hits(rays.shape[0])
+    vol.trace(rays, h1)
+    h2 = vx.alloc_hits(rays.shape[0])
+    vol.render(cam, h2)
+    torch.cuda.synchronize()
+    assert torch.equal(h1, h2)
+    # host variants give the same records
+    hh = vol.render_host(cam)
+    assert np.array_equal(hh, vx.hits_to_numpy(h2))
+    th = vol.trace_host(rays.cpu().numpy())
+    assert np.array_equal(th, vx.hits_to_numpy(h1))
+    # and the compact layout agrees with the full one
+    hc = vol.render_host(cam, layout=vx.HIT_COMPACT)
+    full = vx.hits_to_numpy(h2)
+    k = np.where(full["status"] == 1, full["x"].astype(np.int64) + 128 * (full["y"] + 128 * full["z"].astype(np.int64)), 0xFFFFFFFF)
+    assert np.array_equal(hc["idx"].astype(np.int64), k)
+    assert np.array_equal(hc["t"], full["t"])
+
+
+def test_trace_host_multi_chunk():
+    g = synth.random_grid(51, (64, 64, 64), 0.03)
+    vol = vx.Volume("R(2,2,2) G(4)", g)
+    rays = synth.incoherent_rays(52, 64, (1 << 20) + 12345)
+    h = vol.trace_host(rays)
+    rng = np.random.default_rng(3)
+    s = rng.choice(len(rays), 100000, replace=False)
+    compare(g, rays[s], h[s])
+
+
+def test_bad_arguments_rejected():
+    g = synth.random_grid(61, (16, 16, 16), 0.1)
+    vol = vx.Volume("G(4)", g)
+    rays = torch.zeros((16, 8), device="cuda")
+    hits = vx.alloc_hits(16)
+    with pytest.raises(vx.VxError) as e:
+        vol.trace(rays, hits, layout=7)
+    assert e.value.code == vx.VX_EINVAL
+    with pytest.raises(vx.VxError):
+        vx.lib()  # loaded
+        import ctypes
+        rc = vx.lib().vx_trace(vol.handle, ctypes.c_void_p(rays.data_ptr() + 4), 4,
+                               ctypes.c_void_p(hits.data_ptr()), 0, None, None)
+        vx._check(rc)
+    host_only = vx.Volume("G(4)", g, upload=False)
+    with pytest.raises(vx.VxError):
+        host_only.trace(rays, hits)
