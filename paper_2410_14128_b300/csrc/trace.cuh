@@ -318,6 +318,7 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
     }
     int j = 0;
+    uint32_t Pc = P[0], Mc = M[0];  // node of level j, also kept in P[j], M[j]
     int c[3];
     {
         const int s0 = f.s(0);
@@ -347,25 +348,25 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         bool occ;
         if (kind == K_RAW) {
             idx = lx | (ly << bx) | (lz << (bx + by));
-            w = ldw(pool, P[j] + idx);
+            w = ldw(pool, Pc + idx);
             VX_CNT(bytes, 4);
             occ = w != 0u;
         } else {
             idx = lx | (ly << 1) | (lz << 2);
-            occ = (M[j] >> idx) & 1u;
+            occ = (Mc >> idx) & 1u;
         }
         if (occ) {
             // ---- descend (or hit at the last node level) ----
             uint32_t term = w, Pn = 0, Mn = 0;
             bool node_ready = false;
             if (kind != K_RAW) {
-                const uint32_t rank = __popc(M[j] & ((1u << idx) - 1u));
+                const uint32_t rank = __popc(Mc & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
-                    const uint32_t addr = P[j] + 2u * rank;
+                    const uint32_t addr = Pc + 2u * rank;
                     if (f.bot(j)) { term = ldw(pool, addr); VX_CNT(bytes, 4); }
                     else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
-                    const uint32_t cp = ldw(pool, P[j] + 1u + rank);
+                    const uint32_t cp = ldw(pool, Pc + 1u + rank);
                     if (f.bot(j)) term = ldw(pool, cp);
                     else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
                     VX_CNT(bytes, 8);
@@ -389,6 +390,8 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             ++j;
             P[j] = Pn;
             M[j] = Mn;
+            Pc = Pn;
+            Mc = Mn;
             const int sn = f.s(j), bn = f.b(j);
             const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
 #pragma unroll
@@ -439,6 +442,9 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             a = argmin64(r, pl[0], pl[1], pl[2]);
             tm = tn[a];
         }
+        // A step through the grid's boundary ends the walk whatever the exit
+        // comparison says; only an exit on another axis or at tmax can tie.
+        if (pl[a] == (sg[a] > 0 ? (1 << f.ldim(a)) : 0)) return miss_rec(ST_MISS);
         bool out;
         if (near32(tm, tx)) { VX_CNT(fp64, 1); out = exits64(r, a, pl[a], f.ldim(0), f.ldim(1), f.ldim(2)); }
         else out = !(tm < tx);
@@ -458,6 +464,8 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] >>= sh;
             j = jp;
+            Pc = P[j];
+            Mc = M[j];
         }
     }
     return miss_rec(ST_ERROR);
