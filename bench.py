@@ -87,7 +87,7 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None):
         self.proc = None
         self.out = os.path.join("/tmp", f"vx_clocks_{os.getpid()}.csv")
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if gpu_id:
             cmd += ["-i", gpu_id]
         try:
@@ -167,8 +167,10 @@ def run_reference(args):
     import oracle
     oracle.lib()
     per_step = []
+    # bounded sample per step, so that the whole run stays within a few minutes
+    budget = max(0.05, min(args.ref_step_s, 150.0 / (args.steps + args.warmup)))
     for s in range(args.warmup + args.steps):
-        v, thr, n, t = oracle_rate(grid, cam, inc, budget_s=args.ref_step_s)
+        v, thr, n, t = oracle_rate(grid, cam, inc, budget_s=budget)
         if s >= args.warmup:
             per_step.append((v, n, t))
     rays = sum(p[1] for p in per_step)
@@ -224,7 +226,9 @@ def run_gpu(args):
             counts[(k, name)] = {"node_bytes_per_ray": b / n, "iters_per_ray": it / n, "fp64_per_ray": d / n}
     del prim_rays
 
-    def step(evs=None):
+    mode = {"auto": vx.MODE_AUTO, "plain": vx.MODE_PLAIN, "persistent": vx.MODE_PERSISTENT}[args.mode]
+
+    def step(evs=None, mode=mode):
         flush.zero_()
         for k, v in enumerate(vols):
             if evs is not None:
@@ -233,9 +237,22 @@ def run_gpu(args):
             if evs is not None:
                 evs[(k, "render")][1].record()
                 evs[(k, "trace")][0].record()
-            v.trace(inc, hits_i[k])
+            v.trace(inc, hits_i[k], mode=mode)
             if evs is not None:
                 evs[(k, "trace")][1].record()
+
+    # the plain one-thread-per-ray kernel on the same step, for comparison
+    plain_ms = None
+    if mode != vx.MODE_PLAIN:
+        for _ in range(2):
+            step(mode=vx.MODE_PLAIN)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            step(mode=vx.MODE_PLAIN)
+        b.record()
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b) / 5
 
     for _ in range(args.warmup):
         step()
@@ -363,7 +380,11 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "formats": FORMATS, "rays_per_step": rays_per_step,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"flushed before each step by a {FLUSH_BYTES >> 20} MiB write (inside the timed region)",
-                       "hit_layout": "full 16 B", "mode": "plain (one thread per ray)"},
+                       "hit_layout": "full 16 B",
+                       "mode": {"auto": "auto (persistent warps with ray refill for vx_trace)",
+                                "plain": "plain (one thread per ray)",
+                                "persistent": "persistent warps with ray refill"}[args.mode]},
+            "plain_kernel_ms_per_step": round(plain_ms, 4) if plain_ms else None,
             "per_format": per_format,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -382,9 +403,10 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

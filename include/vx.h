@@ -187,15 +187,21 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *   mode   VX_MODE_*;
  *   block  threads per block: 0 = default, else a multiple of 32 in
  *          [32, 256] (VX_EINVAL otherwise);
- *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = default;
- *   smem_top  1 = stage the top Raw level in shared memory when it fits,
- *          0 = read it from global memory, -1 = default. */
+ *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = as many as fit;
+ *   smem_top  reserved (0);
+ *   refill persistent mode: a warp fetches new rays once this many of its
+ *          lanes are idle (1..32), 0 = default;
+ *   burst  persistent mode: loop iterations between refill checks, 0 = default.
+ * Persistent launches take a queue counter from a ring of 256 per volume, so
+ * up to 256 of them may be in flight at once per volume. */
 typedef struct vx_trace_opts {
     int32_t mode;
     int32_t block;
     int32_t blocks_per_sm;
     int32_t smem_top;
-    int32_t reserved[4];
+    int32_t refill;
+    int32_t burst;
+    int32_t reserved[2];
 } vx_trace_opts;
 
 /* First hit of each ray (Sec. 4.2: the root function reads the root pointer,

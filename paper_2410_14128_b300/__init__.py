@@ -60,7 +60,8 @@ class _Stats(ctypes.Structure):
 
 class _TraceOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("smem_top", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Camera(ctypes.Structure):
@@ -120,9 +121,9 @@ def _check(rc: int):
         raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
 
 
-def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, smem_top=-1):
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0):
     o = _TraceOpts()
-    o.mode, o.block, o.blocks_per_sm, o.smem_top = mode, block, blocks_per_sm, smem_top
+    o.mode, o.block, o.blocks_per_sm, o.smem_top, o.refill, o.burst = mode, block, blocks_per_sm, 0, refill, burst
     return o
 
 

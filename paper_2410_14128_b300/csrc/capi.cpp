@@ -62,6 +62,10 @@ int check_opts(const vx_trace_opts* o) {
     if (o->block != 0 && (o->block < 32 || o->block > 256 || (o->block & 31)))
         return fail(VX_EINVAL, "block must be 0 or a multiple of 32 in [32, 256], got %d", o->block);
     if (o->mode < VX_MODE_AUTO || o->mode > VX_MODE_PERSISTENT) return fail(VX_EINVAL, "bad mode %d", o->mode);
+    if (o->refill < 0 || o->refill > 32) return fail(VX_EINVAL, "refill must be in [0, 32], got %d", o->refill);
+    if (o->burst < 0 || o->burst > 1024) return fail(VX_EINVAL, "burst must be in [0, 1024], got %d", o->burst);
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
+        return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
     return VX_OK;
 }
 
@@ -195,6 +199,8 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
         e = cudaMemcpy(V.d_pool, V.built.words.data(), bytes, cudaMemcpyHostToDevice);
         if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
         V.pool_words = V.built.words.size();
+        e = cudaMalloc((void**)&V.d_queue, kQueueRing * sizeof(unsigned long long));
+        if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMalloc (queue counters)"); }
         st.device_bytes = bytes;
         st.upload_ms = now_ms() - t1;
     }
@@ -211,6 +217,7 @@ extern "C" int vx_free(vx_volume v) {
             cudaDeviceSynchronize();
             cudaFree(v->v.d_pool);
         }
+        if (v->v.d_queue) cudaFree(v->v.d_queue);
         free_staging(v->v.staging);
     }
     delete v;

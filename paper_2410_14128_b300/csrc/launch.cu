@@ -17,7 +17,7 @@ std::vector<const KernelSet*>& registry() {
     return r;
 }
 const KernelSet g_generic = {"*", false, FmtParams{}, &Launch<DynF>::trace, &Launch<DynF>::render,
-                             &Launch<DynF>::trace_count};
+                             &Launch<DynF>::trace_count, &Launch<DynF>::trace_persistent};
 
 CamDev to_dev(const CameraParams& c) {
     CamDev d;
@@ -63,8 +63,20 @@ const KernelSet* kernels_for(const Spec& sp) {
 int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
                  void* stream) {
     const int block = pick_block(o);
-    int e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout, block,
+    const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PERSISTENT;
+    int e;
+    if (mode == VX_MODE_PERSISTENT) {
+        unsigned long long* next = v.queue_counter();
+        if (!next) return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+        const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
+        const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
+        const int bps = o ? o->blocks_per_sm : 0;
+        e = v.kernels->trace_persistent(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout,
+                                        block, bps, refill, burst, (cudaStream_t)stream, next);
+    } else {
+        e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout, block,
                              (cudaStream_t)stream);
+    }
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }

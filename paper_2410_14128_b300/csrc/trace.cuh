@@ -152,25 +152,28 @@ struct Root64 {
 };
 
 // Root slab test in FP64.  Axes with d == 0 were checked by the caller.
-static __device__ __noinline__ Root64 root64(RayIn r, int l0, int l1, int l2) {
+// (Scalar arguments: a struct argument would force the ray into local memory.)
+static __device__ __noinline__ Root64 root64(float o0, float o1, float o2, float d0, float d1, float d2, float tmin,
+                                             float tmax, int l0, int l1, int l2) {
+    const float o[3] = {o0, o1, o2}, d[3] = {d0, d1, d2};
     const int ld[3] = {l0, l1, l2};
     double best = -__longlong_as_double(0x7ff0000000000000ll);
-    double tx = (double)r.tmax;
+    double tx = (double)tmax;
     int e = -1;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        if (r.d[i] == 0.0f) continue;
+        if (d[i] == 0.0f) continue;
         const int n = 1 << ld[i];
-        const int lo = r.d[i] > 0.0f ? 0 : n;
-        const int hi = r.d[i] > 0.0f ? n : 0;
-        const double a = t64(r.o[i], r.d[i], lo);
-        const double b = t64(r.o[i], r.d[i], hi);
+        const int lo = d[i] > 0.0f ? 0 : n;
+        const int hi = d[i] > 0.0f ? n : 0;
+        const double a = t64(o[i], d[i], lo);
+        const double b = t64(o[i], d[i], hi);
         if (a > best) { best = a; e = i; }
         if (b < tx) tx = b;
     }
     Root64 R;
-    if (e >= 0 && best > (double)r.tmin) { R.te = best; R.e = e; }
-    else { R.te = (double)r.tmin; R.e = -1; }
+    if (e >= 0 && best > (double)tmin) { R.te = best; R.e = e; }
+    else { R.te = (double)tmin; R.e = -1; }
     R.tx = tx;
     return R;
 }
@@ -186,30 +189,33 @@ static __device__ __noinline__ int start_coord64(float o, float d, double te) {
 }
 
 // Which of the crossing candidates comes first in FP64 (lowest axis on ties).
-static __device__ __noinline__ int argmin64(RayIn r, int p0, int p1, int p2) {
+static __device__ __noinline__ int argmin64(float o0, float o1, float o2, float d0, float d1, float d2, int p0, int p1,
+                                            int p2) {
+    const float o[3] = {o0, o1, o2}, d[3] = {d0, d1, d2};
     const int pl[3] = {p0, p1, p2};
     int a = -1;
     double m = 0.0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        if (r.d[i] == 0.0f) continue;
-        const double t = t64(r.o[i], r.d[i], pl[i]);
+        if (d[i] == 0.0f) continue;
+        const double t = t64(o[i], d[i], pl[i]);
         if (a < 0 || t < m) { m = t; a = i; }
     }
     return a;
 }
 
-// Is the crossing of `plane` on axis a at or after the exit?
-static __device__ __noinline__ bool exits64(RayIn r, int a, int plane, int l0, int l1, int l2) {
-    const Root64 R = root64(r, l0, l1, l2);
-    return !(t64(r.o[a], r.d[a], plane) < R.tx);
+// Is the crossing time tc (FP64) at or after the exit?
+static __device__ __noinline__ bool exits64(float o0, float o1, float o2, float d0, float d1, float d2, float tmin,
+                                            float tmax, int l0, int l1, int l2, float oa, float da, int plane) {
+    const Root64 R = root64(o0, o1, o2, d0, d1, d2, tmin, tmax, l0, l1, l2);
+    return !(t64(oa, da, plane) < R.tx);
 }
 
 // Has the ray crossed plane B on axis a before the crossing of plane lp on
 // axis la that brought it into the current cell?
-static __device__ __noinline__ bool crossed64(RayIn r, int a, int B, int la, int lp) {
-    const double tb = t64(r.o[a], r.d[a], B);
-    const double tc = t64(r.o[la], r.d[la], lp);
+static __device__ __noinline__ bool crossed64(float oa, float da, int B, int a, float ol, float dl, int lp, int la) {
+    const double tb = t64(oa, da, B);
+    const double tc = t64(ol, dl, lp);
     return tb < tc || (tb == tc && a < la);
 }
 
@@ -222,119 +228,157 @@ __device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint3
 // ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
-template <bool COUNT, class F>
-__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r, Cnt& cnt) {
-#define VX_CNT(field, v) \
-    do {                 \
+#define VX_CNT(field, v)            \
+    do {                            \
         if (COUNT) cnt.field += (v); \
     } while (0)
-    // Invalid rays: any NaN, or an infinite tmin.
-    if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
-        isnan(r.tmin) || isnan(r.tmax) || isinf(r.tmin))
-        return miss_rec(ST_INVALID);
 
+// The traversal state of one ray.  start() does the root part (validity,
+// slab test, start voxel, root node); step() runs one iteration of the loop
+// (one cell lookup with its descent, or one Amanatides-Woo step with its
+// pop).  Both return true once the ray is finished, with the record in `out`.
+// Keeping the state between calls lets a warp swap finished rays for new ones
+// without leaving the loop (persistent kernels).
+template <bool COUNT, class F>
+struct Walker {
+    RayIn r;
+    float inv[3];
+    float tx, tcur;
     int sg[3];
-    float inv[3], nf[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        sg[i] = r.d[i] > 0.0f ? 1 : (r.d[i] < 0.0f ? -1 : 0);
-        inv[i] = __frcp_rn(r.d[i]);
-        nf[i] = (float)(1 << f.ldim(i));
-    }
+    int v0[3], c[3];
+    int j, la, lp, it;
+    bool fresh;
+    uint32_t Pc, Mc;  // node of level j (also kept in P[j], M[j])
+    uint32_t* P;      // per-level node stack, F::kMaxJ entries each, owned by
+    uint32_t* M;      // the caller (kept outside so the scalars stay in registers)
+    Cnt cnt;
 
-    // ---- root slab test (FP32, FP64 when undecided) ----
-    float t0[3], best = -__int_as_float(0x7f800000), tx = r.tmax;
-    int e = -1;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        t0[i] = 0.0f;
-        if (sg[i] == 0) {
-            if (!(r.o[i] >= 0.0f && r.o[i] < nf[i])) return miss_rec(ST_MISS);
-            continue;
+    __device__ __forceinline__ bool start(const F& f, const uint32_t* __restrict__ pool, const RayIn& ray,
+                                          HitRec& out) {
+        r = ray;
+        // Invalid rays: any NaN, or an infinite tmin.
+        if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
+            isnan(r.tmin) || isnan(r.tmax) || isinf(r.tmin)) {
+            out = miss_rec(ST_INVALID);
+            return true;
         }
-        const float lo = sg[i] > 0 ? 0.0f : nf[i];
-        const float hi = sg[i] > 0 ? nf[i] : 0.0f;
-        t0[i] = (lo - r.o[i]) * inv[i];
-        const float t1 = (hi - r.o[i]) * inv[i];
-        if (t0[i] > best) { best = t0[i]; e = i; }
-        tx = fminf(tx, t1);
-    }
-    bool unsure = false;
+        float nf[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++)
-        if (sg[i] != 0 && i != e && near32(t0[i], best)) unsure = true;
-    if (e >= 0 && near32(best, r.tmin)) unsure = true;
-    int ea;
-    float te;
-    if (e >= 0 && best > r.tmin) { te = best; ea = e; }
-    else { te = r.tmin; ea = -1; }
-    bool miss;
-    if (unsure || near32(te, tx)) {
-        VX_CNT(fp64, 1);
-        const Root64 R = root64(r, f.ldim(0), f.ldim(1), f.ldim(2));
-        ea = R.e;
-        te = (float)R.te;
-        tx = (float)R.tx;
-        miss = !(R.te < R.tx);
-    } else {
-        miss = !(te < tx);
-    }
-    if (miss) return miss_rec(ST_MISS);
+        for (int i = 0; i < 3; i++) {
+            sg[i] = r.d[i] > 0.0f ? 1 : (r.d[i] < 0.0f ? -1 : 0);
+            inv[i] = __frcp_rn(r.d[i]);
+            nf[i] = (float)(1 << f.ldim(i));
+        }
 
-    // ---- start voxel ----
-    int v0[3];
+        // ---- root slab test (FP32, FP64 when undecided) ----
+        float t0[3], best = -__int_as_float(0x7f800000);
+        tx = r.tmax;
+        int e = -1;
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const int n = 1 << f.ldim(i);
-        int v;
-        if (i == ea) {
-            v = sg[i] > 0 ? 0 : n - 1;
+        for (int i = 0; i < 3; i++) {
+            t0[i] = 0.0f;
+            if (sg[i] == 0) {
+                if (!(r.o[i] >= 0.0f && r.o[i] < nf[i])) {
+                    out = miss_rec(ST_MISS);
+                    return true;
+                }
+                continue;
+            }
+            const float lo = sg[i] > 0 ? 0.0f : nf[i];
+            const float hi = sg[i] > 0 ? nf[i] : 0.0f;
+            t0[i] = (lo - r.o[i]) * inv[i];
+            const float t1 = (hi - r.o[i]) * inv[i];
+            if (t0[i] > best) { best = t0[i]; e = i; }
+            tx = fminf(tx, t1);
+        }
+        bool unsure = false;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            if (sg[i] != 0 && i != e && near32(t0[i], best)) unsure = true;
+        if (e >= 0 && near32(best, r.tmin)) unsure = true;
+        int ea;
+        float te;
+        if (e >= 0 && best > r.tmin) { te = best; ea = e; }
+        else { te = r.tmin; ea = -1; }
+        bool miss;
+        if (unsure || near32(te, tx)) {
+            VX_CNT(fp64, 1);
+            const Root64 R = root64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0),
+                                    f.ldim(1), f.ldim(2));
+            ea = R.e;
+            te = (float)R.te;
+            tx = (float)R.tx;
+            miss = !(R.te < R.tx);
         } else {
-            const float p = fmaf(te, r.d[i], r.o[i]);
-            const float fl = floorf(p);
-            v = (int)fminf(fmaxf(fl, -2.0f), 65536.0f);
-            if (sg[i] != 0) {
-                const float rq = rintf(p);
-                if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
-                    VX_CNT(fp64, 1);
-                    const double te64 = ea >= 0 ? t64(r.o[ea], r.d[ea], sg[ea] > 0 ? 0 : (1 << f.ldim(ea)))
-                                                : (double)r.tmin;
-                    v = start_coord64(r.o[i], r.d[i], te64);
+            miss = !(te < tx);
+        }
+        if (miss) {
+            out = miss_rec(ST_MISS);
+            return true;
+        }
+
+        // ---- start voxel ----
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int n = 1 << f.ldim(i);
+            int v;
+            if (i == ea) {
+                v = sg[i] > 0 ? 0 : n - 1;
+            } else {
+                const float p = fmaf(te, r.d[i], r.o[i]);
+                const float fl = floorf(p);
+                v = (int)fminf(fmaxf(fl, -2.0f), 65536.0f);
+                if (sg[i] != 0) {
+                    const float rq = rintf(p);
+                    if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
+                        VX_CNT(fp64, 1);
+                        const double te64 = ea >= 0 ? t64(r.o[ea], r.d[ea], sg[ea] > 0 ? 0 : (1 << f.ldim(ea)))
+                                                    : (double)r.tmin;
+                        v = start_coord64(r.o[i], r.d[i], te64);
+                    }
                 }
             }
+            v0[i] = min(max(v, 0), n - 1);
         }
-        v0[i] = min(max(v, 0), n - 1);
-    }
 
-    // ---- root node ----
-    const uint32_t root = ldw(pool, 0);
-    VX_CNT(bytes, 4);
-    if (root == 0) return miss_rec(ST_MISS);
-    uint32_t P[F::kMaxJ], M[F::kMaxJ];
-    {
-        const int k0 = f.kind(0);
-        if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
-        else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
-        else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
-    }
-    int j = 0;
-    uint32_t Pc = P[0], Mc = M[0];  // node of level j, also kept in P[j], M[j]
-    int c[3];
-    {
-        const int s0 = f.s(0);
+        // ---- root node ----
+        const uint32_t root = ldw(pool, 0);
+        VX_CNT(bytes, 4);
+        if (root == 0) {
+            out = miss_rec(ST_MISS);
+            return true;
+        }
+        {
+            const int k0 = f.kind(0);
+            if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
+            else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+            else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
+        }
+        j = 0;
+        Pc = P[0];
+        Mc = M[0];
+        {
+            const int s0 = f.s(0);
 #pragma unroll
-        for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
+            for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
+        }
+        la = ea;                                                  // axis of the last crossing
+        lp = ea >= 0 ? (sg[ea] > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
+        tcur = te;
+        fresh = true;  // no step taken yet
+        it = 0;
+        return false;
     }
-    int la = ea;                                          // axis of the last crossing
-    int lp = ea >= 0 ? (sg[ea] > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
-    float tcur = te;
-    bool fresh = true;                                    // no step taken yet
-    const int J = f.J();
-    // A ray crosses at most nx + ny + nz cells of any level and each step
-    // costs at most J descents; past this bound the ray reports ST_ERROR.
-    const int cap = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (J + 2);
 
-    for (int it = 0; it < cap; ++it) {
+    __device__ __forceinline__ bool step(const F& f, const uint32_t* __restrict__ pool, HitRec& out) {
+        // A ray crosses at most nx + ny + nz cells of any level and each step
+        // costs at most J descents; past this bound the ray reports ST_ERROR.
+        const int J = f.J();
+        const int cap = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (J + 2);
+        if (++it > cap) {
+            out = miss_rec(ST_ERROR);
+            return true;
+        }
         VX_CNT(iters, 1);
         const int kind = f.kind(j);
         const int s = f.s(j);
@@ -373,13 +417,12 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
                 }
             }
             if (j == J - 1) {
-                HitRec h;
-                h.t = tcur;
-                h.rgba = term;
-                h.x = c[0]; h.y = c[1]; h.z = c[2];
-                h.face = la >= 0 ? 1 + 2 * la + (sg[la] < 0 ? 1 : 0) : 0;
-                h.status = ST_HIT;
-                return h;
+                out.t = tcur;
+                out.rgba = term;
+                out.x = c[0]; out.y = c[1]; out.z = c[2];
+                out.face = la >= 0 ? 1 + 2 * la + (sg[la] < 0 ? 1 : 0) : 0;
+                out.status = ST_HIT;
+                return true;
             }
             if (!node_ready) {
                 const int nk = f.kind(j + 1);
@@ -409,13 +452,13 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
                     fabsf(q - rq) <= kGuard * (fabsf(tcur * r.d[i]) + fabsf(p)) * scale) {
                     VX_CNT(fp64, 1);
                     const int B = (int)rq;
-                    const bool cr = crossed64(r, i, B << sn, la, lp);
+                    const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, r.o[la], r.d[la], lp, la);
                     cn = sg[i] > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
                 }
                 const int vs = v0[i] >> sn;
                 c[i] = sg[i] > 0 ? max(cn, vs) : min(cn, vs);
             }
-            continue;
+            return false;
         }
 
         // ---- one Amanatides-Woo step at node level j ----
@@ -430,8 +473,9 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         float tm = tn[0];
         if (tn[1] < tm) { a = 1; tm = tn[1]; }
         if (tn[2] < tm) { a = 2; tm = tn[2]; }
-        if (!(tm < __int_as_float(0x7f800000))) {
-            if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) return miss_rec(ST_MISS);
+        if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) {
+            out = miss_rec(ST_MISS);
+            return true;
         }
         bool und = false;
 #pragma unroll
@@ -439,16 +483,21 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             if (sg[i] != 0 && i != a && near32(tm, tn[i])) und = true;
         if (und) {
             VX_CNT(fp64, 1);
-            a = argmin64(r, pl[0], pl[1], pl[2]);
+            a = argmin64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], pl[0], pl[1], pl[2]);
             tm = tn[a];
         }
         // A step through the grid's boundary ends the walk whatever the exit
         // comparison says; only an exit on another axis or at tmax can tie.
-        if (pl[a] == (sg[a] > 0 ? (1 << f.ldim(a)) : 0)) return miss_rec(ST_MISS);
-        bool out;
-        if (near32(tm, tx)) { VX_CNT(fp64, 1); out = exits64(r, a, pl[a], f.ldim(0), f.ldim(1), f.ldim(2)); }
-        else out = !(tm < tx);
-        if (out) return miss_rec(ST_MISS);
+        bool out_now = pl[a] == (sg[a] > 0 ? (1 << f.ldim(a)) : 0);
+        if (!out_now) {
+            if (near32(tm, tx)) { VX_CNT(fp64, 1); out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
+                                                     f.ldim(2), r.o[a], r.d[a], pl[a]); }
+            else out_now = !(tm < tx);
+        }
+        if (out_now) {
+            out = miss_rec(ST_MISS);
+            return true;
+        }
         const int old = c[a];
         c[a] += sg[a];
         tcur = tm;
@@ -458,7 +507,10 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
         const int h = 31 - __clz((uint32_t)(old ^ c[a])) + s;  // highest changed voxel-coordinate bit
         const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
         if (h >= span) {
-            if (h >= f.ldim(a)) return miss_rec(ST_MISS);
+            if (h >= f.ldim(a)) {
+                out = miss_rec(ST_MISS);
+                return true;
+            }
             const int jp = f.jpop(h);
             const int sh = f.s(jp) - s;
 #pragma unroll
@@ -467,9 +519,27 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restri
             Pc = P[j];
             Mc = M[j];
         }
+        return false;
     }
-    return miss_rec(ST_ERROR);
+};
 #undef VX_CNT
+
+template <bool COUNT, class F>
+__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r, Cnt& cnt) {
+    uint32_t P[F::kMaxJ], M[F::kMaxJ];
+    Walker<COUNT, F> w;
+    w.P = P;
+    w.M = M;
+    HitRec h;
+    if (!w.start(f, pool, r, h))
+        while (!w.step(f, pool, h)) {
+        }
+    if (COUNT) {
+        cnt.bytes += w.cnt.bytes;
+        cnt.iters += w.cnt.iters;
+        cnt.fp64 += w.cnt.fp64;
+    }
+    return h;
 }
 
 // ---------------------------------------------------------------------------
@@ -569,6 +639,59 @@ __global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __rest
 }
 
 // Pixels i0 .. i0 + n - 1 (index px + W py); hit k of the launch is pixel i0 + k.
+// Persistent variant (one launch fills the GPU; warps stay resident).  When
+// at least `refill` lanes of a warp are idle, the warp takes that many new
+// rays from the global queue counter `next` with one atomic and hands them to
+// the idle lanes in lane order (ballot + popc rank + shuffle); busy lanes keep
+// walking.  Each round advances every live lane by up to `burst` iterations.
+// `next` must be zero at launch; the kernel leaves it >= n.
+template <class F, int LAYOUT>
+__global__ void __launch_bounds__(256) k_trace_persistent(F f, const uint32_t* __restrict__ pool,
+                                                          const float4* __restrict__ rays, uint64_t n,
+                                                          void* __restrict__ hits, unsigned long long* next,
+                                                          int refill, int burst) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t P[F::kMaxJ], M[F::kMaxJ];
+    Walker<false, F> w;
+    w.P = P;
+    w.M = M;
+    bool live = false;
+    bool exhausted = false;  // warp-uniform
+    uint64_t idx = 0;
+    while (true) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !live);
+        if (exhausted) {
+            if (idle == 0xffffffffu) break;
+        } else if (__popc(idle) >= refill) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(next, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (base + (unsigned long long)__popc(idle) >= n) exhausted = true;
+            if (!live) {
+                idx = base + __popc(idle & lt_mask);
+                if (idx < n) {
+                    HitRec h;
+                    if (w.start(f, pool, load_ray(rays, idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
+                    else live = true;
+                }
+            }
+            continue;  // re-evaluate the warp's state before stepping
+        }
+        if (live) {
+            for (int k = 0; k < burst; k++) {
+                HitRec h;
+                if (w.step(f, pool, h)) {
+                    store_hit<LAYOUT>(f, hits, idx, h);
+                    live = false;
+                    break;
+                }
+            }
+        }
+    }
+}
+
 template <class F, int LAYOUT>
 __global__ void __launch_bounds__(256) k_render(F f, const uint32_t* __restrict__ pool, CamDev cam, uint64_t i0,
                                                 uint64_t n, void* __restrict__ hits) {
@@ -594,6 +717,9 @@ struct KernelSet {
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
                        int layout, int block, cudaStream_t st, unsigned long long* counters);
+    int (*trace_persistent)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+                            int layout, int block, int blocks_per_sm, int refill, int burst, cudaStream_t st,
+                            unsigned long long* next);
 };
 
 template <class F>
@@ -615,6 +741,34 @@ struct Launch {
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
         if (layout == 0) k_trace_count<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         else k_trace_count<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+        return (int)cudaGetLastError();
+    }
+    // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
+    static int trace_persistent(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+                                int layout, int block, int blocks_per_sm, int refill, int burst, cudaStream_t st,
+                                unsigned long long* next) {
+        if (n == 0) return 0;
+        const F f = make(p);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = blocks_per_sm;
+        if (per_sm <= 0) {
+            cudaError_t e = layout == 0
+                                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0>, block, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1>, block, 0);
+            if (e) return (int)e;
+            if (per_sm < 1) per_sm = 1;
+        }
+        uint64_t grid = (uint64_t)sms * per_sm;
+        const uint64_t need = (n + (uint64_t)block - 1) / (uint64_t)block;
+        if (grid > need) grid = need;
+        cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+        if (e) return (int)e;
+        if (layout == 0)
+            k_trace_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, next, refill, burst);
+        else
+            k_trace_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -642,7 +796,8 @@ inline F Launch<F>::make(const FmtParams&) {
 template <class Fm>
 KernelSet make_kernel_set(const char* spec) {
     using F = typename Fm::F;
-    return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render, &Launch<F>::trace_count};
+    return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render, &Launch<F>::trace_count,
+                     &Launch<F>::trace_persistent};
 }
 
 void register_kernel_set(const KernelSet* ks);

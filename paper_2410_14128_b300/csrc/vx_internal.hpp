@@ -3,6 +3,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <atomic>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -94,6 +95,10 @@ struct Staging {
     void* ready = nullptr;
 };
 
+constexpr int kDefaultRefill = 8;  // persistent kernel: idle lanes before a warp refills
+constexpr int kDefaultBurst = 4;   // persistent kernel: iterations between refill checks
+constexpr int kQueueRing = 256;    // queue counters per volume
+
 struct Volume {
     Spec spec;
     BuildResult built;
@@ -104,6 +109,12 @@ struct Volume {
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
     Staging staging;
+    unsigned long long* d_queue = nullptr;  // kQueueRing counters
+    mutable std::atomic<uint32_t> queue_slot{0};
+    unsigned long long* queue_counter() const {
+        if (!d_queue) return nullptr;
+        return d_queue + (queue_slot.fetch_add(1, std::memory_order_relaxed) % kQueueRing);
+    }
 };
 
 const KernelSet* kernels_for(const Spec& sp);

@@ -244,3 +244,40 @@ def test_bad_arguments_rejected():
     host_only = vx.Volume("G(4)", g, upload=False)
     with pytest.raises(vx.VxError):
         host_only.trace(rays, hits)
+
+
+# ---------------------------------------------------------------------------
+# Persistent kernel (warp refill from a global ray queue) == plain kernel
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "R(2,2,2) R(2,2,2) R(3,3,3)", "G(7)", "S(1) G(2) R(2,2,2) S(2)"])
+def test_persistent_equals_plain(spec):
+    g = synth.terrain_volume(71, 128)
+    rays = np.concatenate([synth.incoherent_rays(72, 128, 70001), lattice_rays(73, (128, 128, 128), 5000)])
+    vol = vx.Volume(spec, g)
+    plain = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    compare(g, rays, plain)
+    for refill, burst, block, bps in [(1, 1, 256, 0), (8, 4, 256, 0), (32, 16, 128, 0), (16, 2, 64, 1),
+                                      (4, 64, 32, 0)]:
+        got = gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, refill=refill, burst=burst, block=block,
+                        blocks_per_sm=bps)
+        assert np.array_equal(got, plain), (refill, burst, block, bps)
+
+
+def test_persistent_small_and_repeated():
+    g = synth.random_grid(74, (32, 32, 32), 0.1)
+    vol = vx.Volume("R(2,2,2) G(3)", g)
+    for n in (1, 5, 33, 1000):
+        rays = synth.aimed_rays(75 + n, (32, 32, 32), n)
+        compare(g, rays, gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT))
+    # many launches in a row reuse the ring of queue counters
+    rays = synth.aimed_rays(80, (32, 32, 32), 3000)
+    r = torch.from_numpy(rays).cuda()
+    ref = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    hs = [vx.alloc_hits(len(rays)) for _ in range(300)]
+    for h in hs:
+        vol.trace(r, h, mode=vx.MODE_PERSISTENT)
+    torch.cuda.synchronize()
+    for h in hs[::37]:
+        assert np.array_equal(vx.hits_to_numpy(h), ref)
+    with pytest.raises(vx.VxError):
+        gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, refill=33)
