@@ -232,6 +232,26 @@ int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, in
 int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,
                   const vx_trace_opts* opts, void* stream);
 
+/* vx_trace for callers that cannot allocate device memory while tracing:
+ * applications whose own allocator owns the GPU's memory, real-time loops
+ * that forbid allocation (and the synchronisation it implies) after start-up,
+ * plug-ins whose host manages device memory.  The paper has no counterpart;
+ * this is a service of the library.
+ * Same hits as vx_trace (the persistent kernel, format described at run time).
+ * Its only scratch, a 32-bit ray-queue counter, sits in a 256-byte static
+ * device array that every GPU which loads the library keeps until the process
+ * exits; the call itself never calls cudaMalloc or cudaFree.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current: make that first call
+ *     before any stream capture.
+ *   - All calls share the array; each zeroes the counter on its stream before
+ *     its launch, so calls whose kernels overlap on the GPU race: issue them
+ *     one after another (e.g. on one stream).
+ *   - n must not exceed VX_NOALLOC_MAX_RAYS (VX_EINVAL otherwise).
+ * Arguments and errors otherwise as vx_trace (block size and mode fixed). */
+#define VX_NOALLOC_MAX_RAYS 4278190080ull /* 2^32 - 2^24 */
+int vx_trace_noalloc(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout, void* stream);
+
 /* ----------------------------------------------------------------------- */
 /* Ray generation                                                           */
 /* ----------------------------------------------------------------------- */

@@ -21,6 +21,7 @@ MODE_AUTO, MODE_PLAIN, MODE_PERSISTENT = 0, 1, 2
 STATUS_MISS, STATUS_HIT, STATUS_INVALID, STATUS_ERROR = 0, 1, 2, 3
 DEDUP_PER_SUBVOLUME, DEDUP_WHOLE_LEVEL = 0, 1
 MAX_LEVELS = 16
+NOALLOC_MAX_RAYS = 4278190080
 
 HIT_DTYPE = np.dtype([("t", "<f4"), ("rgba", "<u4"), ("x", "<u2"), ("y", "<u2"), ("z", "<u2"),
                       ("face", "u1"), ("status", "u1")])
@@ -86,6 +87,8 @@ _SIGS = {
                                         ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                      ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_trace_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p]),
     "vx_raygen_pinhole": (ctypes.c_int, [ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_void_p]),
     "vx_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),

@@ -303,6 +303,16 @@ extern "C" int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, v
     });
 }
 
+extern "C" int vx_trace_noalloc(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
+                                void* stream) {
+    clear_error();
+    int rc = check_trace_args(v, rays, n, hits, hit_layout);
+    if (rc) return rc;
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return trace_noalloc(v->v, rays, n, hits, hit_layout, stream);
+}
+
 extern "C" int vx_raygen_pinhole(const vx_camera* cam, vx_ray* rays, void* stream) {
     clear_error();
     CameraParams cp;

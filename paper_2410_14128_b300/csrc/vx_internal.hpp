@@ -132,6 +132,7 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
+int trace_noalloc(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, void* stream);
 int camera_params(const vx_camera* cam, CameraParams* out);
 
 }  // namespace vx
