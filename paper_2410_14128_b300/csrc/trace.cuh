@@ -219,6 +219,13 @@ static __device__ __noinline__ bool crossed64(float oa, float da, int B, int a, 
     return tb < tc || (tb == tc && a < la);
 }
 
+// Element i of a 3-array, by selects: a runtime index into a small array
+// would move the array to local memory.
+template <class T>
+__device__ __forceinline__ T sel3(const T (&v)[3], int i) {
+    return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+}
+
 __device__ __forceinline__ bool near32(float x, float y) {
     return !(fabsf(x - y) > kGuard * fmaxf(fabsf(x), fabsf(y)));
 }
@@ -332,7 +339,8 @@ struct Walker {
                     const float rq = rintf(p);
                     if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
                         VX_CNT(fp64, 1);
-                        const double te64 = ea >= 0 ? t64(r.o[ea], r.d[ea], sg[ea] > 0 ? 0 : (1 << f.ldim(ea)))
+                        const double te64 = ea >= 0 ? t64(sel3(r.o, ea), sel3(r.d, ea),
+                                                          sel3(sg, ea) > 0 ? 0 : (1 << f.ldim(ea)))
                                                     : (double)r.tmin;
                         v = start_coord64(r.o[i], r.d[i], te64);
                     }
@@ -362,8 +370,8 @@ struct Walker {
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
         }
-        la = ea;                                                  // axis of the last crossing
-        lp = ea >= 0 ? (sg[ea] > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
+        la = ea;                                                        // axis of the last crossing
+        lp = ea >= 0 ? (sel3(sg, ea) > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
         tcur = te;
         fresh = true;  // no step taken yet
         it = 0;
@@ -420,7 +428,7 @@ struct Walker {
                 out.t = tcur;
                 out.rgba = term;
                 out.x = c[0]; out.y = c[1]; out.z = c[2];
-                out.face = la >= 0 ? 1 + 2 * la + (sg[la] < 0 ? 1 : 0) : 0;
+                out.face = la >= 0 ? 1 + 2 * la + (sel3(sg, la) < 0 ? 1 : 0) : 0;
                 out.status = ST_HIT;
                 return true;
             }
@@ -452,7 +460,7 @@ struct Walker {
                     fabsf(q - rq) <= kGuard * (fabsf(tcur * r.d[i]) + fabsf(p)) * scale) {
                     VX_CNT(fp64, 1);
                     const int B = (int)rq;
-                    const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, r.o[la], r.d[la], lp, la);
+                    const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, sel3(r.o, la), sel3(r.d, la), lp, la);
                     cn = sg[i] > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
                 }
                 const int vs = v0[i] >> sn;
@@ -484,27 +492,35 @@ struct Walker {
         if (und) {
             VX_CNT(fp64, 1);
             a = argmin64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], pl[0], pl[1], pl[2]);
-            tm = tn[a];
+            tm = sel3(tn, a);
         }
         // A step through the grid's boundary ends the walk whatever the exit
         // comparison says; only an exit on another axis or at tmax can tie.
-        bool out_now = pl[a] == (sg[a] > 0 ? (1 << f.ldim(a)) : 0);
+        const int pla = sel3(pl, a), sga = sel3(sg, a);
+        bool out_now = pla == (sga > 0 ? (1 << f.ldim(a)) : 0);
         if (!out_now) {
-            if (near32(tm, tx)) { VX_CNT(fp64, 1); out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
-                                                     f.ldim(2), r.o[a], r.d[a], pl[a]); }
-            else out_now = !(tm < tx);
+            if (near32(tm, tx)) {
+                VX_CNT(fp64, 1);
+                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
+                                  f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
+            } else {
+                out_now = !(tm < tx);
+            }
         }
         if (out_now) {
             out = miss_rec(ST_MISS);
             return true;
         }
-        const int old = c[a];
-        c[a] += sg[a];
+        const int old = sel3(c, a);
+        const int nw = old + sga;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            if (i == a) c[i] = nw;
         tcur = tm;
         la = a;
-        lp = pl[a];
+        lp = pla;
         fresh = false;
-        const int h = 31 - __clz((uint32_t)(old ^ c[a])) + s;  // highest changed voxel-coordinate bit
+        const int h = 31 - __clz((uint32_t)(old ^ nw)) + s;  // highest changed voxel-coordinate bit
         const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
         if (h >= span) {
             if (h >= f.ldim(a)) {
@@ -646,7 +662,7 @@ __global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __rest
 // walking.  Each round advances every live lane by up to `burst` iterations.
 // `next` must be zero at launch; the kernel leaves it >= n.
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256) k_trace_persistent(F f, const uint32_t* __restrict__ pool,
+__global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t* __restrict__ pool,
                                                           const float4* __restrict__ rays, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
                                                           int refill, int burst) {
