@@ -211,6 +211,13 @@ def run_gpu(args):
     hits_i = [vx.alloc_hits(N_INC) for _ in FORMATS]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     rays_per_step = len(FORMATS) * (n_prim + N_INC)
+    mode = {"auto": vx.MODE_AUTO, "plain": vx.MODE_PLAIN, "persistent": vx.MODE_PERSISTENT}[args.mode]
+
+    # --- autotune the incoherent-ray trace per format (outside timing) ---
+    tuned = []
+    if mode == vx.MODE_AUTO and not args.no_tune:
+        for v in vols:
+            tuned.append(v.autotune(inc[: 1 << 19]))
 
     # --- algorithmic bytes per ray (instrumented kernels, outside timing) ---
     counts = {}
@@ -225,8 +232,6 @@ def run_gpu(args):
             n = rays.shape[0]
             counts[(k, name)] = {"node_bytes_per_ray": b / n, "iters_per_ray": it / n, "fp64_per_ray": d / n}
     del prim_rays
-
-    mode = {"auto": vx.MODE_AUTO, "plain": vx.MODE_PLAIN, "persistent": vx.MODE_PERSISTENT}[args.mode]
 
     def step(evs=None, mode=mode):
         flush.zero_()
@@ -317,6 +322,7 @@ def run_gpu(args):
             "iters_per_ray_incoherent": round(counts[(k, "trace")]["iters_per_ray"], 2),
             "fp64_decisions_per_ray_incoherent": round(counts[(k, "trace")]["fp64_per_ray"], 5),
             "specialized_kernel": st["specialized"],
+            "tuned_trace_opts": tuned[k] if tuned else None,
         })
     dom = max(tot, key=tot.get)
     k, name = dom
@@ -381,7 +387,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"flushed before each step by a {FLUSH_BYTES >> 20} MiB write (inside the timed region)",
                        "hit_layout": "full 16 B",
-                       "mode": {"auto": "auto (persistent warps with ray refill for vx_trace)",
+                       "mode": {"auto": "auto (vx_trace options autotuned per format on 2^19 of the rays)",
                                 "plain": "plain (one thread per ray)",
                                 "persistent": "persistent warps with ray refill"}[args.mode]},
             "plain_kernel_ms_per_step": round(plain_ms, 4) if plain_ms else None,
@@ -408,6 +414,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)

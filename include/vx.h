@@ -191,7 +191,13 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *   smem_top  reserved (0);
  *   refill persistent mode: a warp fetches new rays once this many of its
  *          lanes are idle (1..32), 0 = default;
- *   burst  persistent mode: loop iterations between refill checks, 0 = default.
+ *   burst  persistent mode: loop iterations between refill checks, 0 = default;
+ *   sort_cell_log2  0 = trace rays in the given order; g in [1, 15] = first
+ *          sort them by (direction octant, Morton code of the origin's cell of
+ *          side 2^g) for coherence; hits still land in the caller's order.
+ *          Sorting takes 8 B per ray plus up to 1 MiB of device scratch from
+ *          CUDA's stream-ordered allocator (cudaMallocAsync), at most 2^32 - 1
+ *          rays per call.
  * Persistent launches take a queue counter from a ring of 256 per volume, so
  * up to 256 of them may be in flight at once per volume. */
 typedef struct vx_trace_opts {
@@ -201,7 +207,8 @@ typedef struct vx_trace_opts {
     int32_t smem_top;
     int32_t refill;
     int32_t burst;
-    int32_t reserved[2];
+    int32_t sort_cell_log2;
+    int32_t reserved;
 } vx_trace_opts;
 
 /* First hit of each ray (Sec. 4.2: the root function reads the root pointer,
@@ -225,6 +232,17 @@ int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hi
  * algorithmic traffic of the method. */
 int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
                      const vx_trace_opts* opts, void* stream, unsigned long long* counters);
+
+/* Picks vx_trace options for this volume: times candidates on `rays` (a
+ * device sample of the rays the caller will trace, n of them) with CUDA
+ * events on `stream` -- persistent refill threshold, iterations per refill
+ * check, block size, coherence-sort granularity, plain vs persistent -- by
+ * coordinate descent, and keeps the fastest; later vx_trace calls with
+ * opts NULL or mode VX_MODE_AUTO use it.  Synchronises `stream`; allocates a
+ * temporary n-hit buffer.  best (optional) receives the options, best_ms the
+ * sample's time with them.  (Not in the paper: its formats are traced with
+ * one fixed GLSL shader per format.) */
+int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* stream, vx_trace_opts* best, double* best_ms);
 
 /* Same as vx_trace with host arrays: the rays are copied to the device in
  * chunks, traced and the hits copied back, copies overlapped with tracing.

@@ -62,7 +62,7 @@ class _Stats(ctypes.Structure):
 class _TraceOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("sort_cell_log2", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Camera(ctypes.Structure):
@@ -85,6 +85,8 @@ _SIGS = {
                                 ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_trace_counted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p]),
+    "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                   ctypes.POINTER(_TraceOpts), ctypes.POINTER(ctypes.c_double)]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                      ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_trace_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -124,9 +126,10 @@ def _check(rc: int):
         raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
 
 
-def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0):
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0):
     o = _TraceOpts()
     o.mode, o.block, o.blocks_per_sm, o.smem_top, o.refill, o.burst = mode, block, blocks_per_sm, 0, refill, burst
+    o.sort_cell_log2 = sort
     return o
 
 
@@ -268,6 +271,16 @@ class Volume:
                                       layout, ctypes.byref(o), _stream_handle(stream),
                                       ctypes.c_void_p(counters.data_ptr())))
         return hits
+
+    def autotune(self, sample_rays, stream=None) -> dict:
+        """Times trace options on a device sample of rays; vx_trace with the
+        default mode then uses the fastest.  Returns the options and time."""
+        o = _TraceOpts()
+        ms = ctypes.c_double()
+        _check(lib().vx_autotune(self._h, ctypes.c_void_p(sample_rays.data_ptr()), sample_rays.shape[0],
+                                 _stream_handle(stream), ctypes.byref(o), ctypes.byref(ms)))
+        return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
+                "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "sample_ms": ms.value}
 
     def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,
                    **opts) -> np.ndarray:

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <memory>
 
@@ -64,6 +65,8 @@ int check_opts(const vx_trace_opts* o) {
     if (o->mode < VX_MODE_AUTO || o->mode > VX_MODE_PERSISTENT) return fail(VX_EINVAL, "bad mode %d", o->mode);
     if (o->refill < 0 || o->refill > 32) return fail(VX_EINVAL, "refill must be in [0, 32], got %d", o->refill);
     if (o->burst < 0 || o->burst > 1024) return fail(VX_EINVAL, "burst must be in [0, 1024], got %d", o->burst);
+    if (o->sort_cell_log2 < 0 || o->sort_cell_log2 > 15)
+        return fail(VX_EINVAL, "sort_cell_log2 must be in [0, 15], got %d", o->sort_cell_log2);
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
         return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
     return VX_OK;
@@ -278,6 +281,87 @@ extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, voi
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
     return launch_trace_count(v->v, rays, n, hits, hit_layout, opts, stream, counters);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: coordinate descent over the trace options, each candidate timed
+// with CUDA events on the sample (best of 3 runs after one warm-up run).
+// ---------------------------------------------------------------------------
+namespace {
+
+int time_opts(Volume& V, const vx_ray* rays, uint64_t n, void* hits, const vx_trace_opts& o, cudaStream_t st,
+              cudaEvent_t a, cudaEvent_t b, float* ms) {
+    int rc = launch_trace(V, rays, n, hits, VX_HIT_FULL, &o, st);
+    if (rc) return rc;
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+        cudaEventRecord(a, st);
+        rc = launch_trace(V, rays, n, hits, VX_HIT_FULL, &o, st);
+        if (rc) return rc;
+        cudaEventRecord(b, st);
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e) return cuda_fail(e, "autotune");
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, a, b);
+        if (t < best) best = t;
+    }
+    *ms = best;
+    return VX_OK;
+}
+
+}  // namespace
+
+extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* stream, vx_trace_opts* best_out,
+                           double* best_ms) {
+    clear_error();
+    int rc = check_trace_args(v, rays, n, nullptr, VX_HIT_FULL);
+    if (rc) return rc;
+    if (n == 0 || !rays) return fail(VX_EINVAL, "autotune needs a non-empty sample of rays");
+    if (!aligned(rays, 16)) return fail(VX_EINVAL, "rays must be 16-byte aligned");
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    Volume& V = v->v;
+    cudaStream_t st = (cudaStream_t)stream;
+    void* hits = nullptr;
+    cudaError_t e = cudaMalloc(&hits, n * sizeof(vx_hit));
+    if (e) return cuda_fail(e, "cudaMalloc (autotune hits)");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    vx_trace_opts cur{};
+    cur.mode = VX_MODE_PERSISTENT;
+    cur.block = 256;
+    cur.refill = kDefaultRefill;
+    cur.burst = kDefaultBurst;
+    float cur_ms = 0.0f;
+    rc = time_opts(V, rays, n, hits, cur, st, a, b, &cur_ms);
+    auto consider = [&](vx_trace_opts cand) {
+        if (rc) return;
+        float ms = 0.0f;
+        rc = time_opts(V, rays, n, hits, cand, st, a, b, &ms);
+        if (!rc && ms < cur_ms) { cur = cand; cur_ms = ms; }
+    };
+    const int maxg = std::min(V.spec.ldim[0], std::min(V.spec.ldim[1], V.spec.ldim[2]));
+    for (int g : {2, 3, 4, 5, 6, 7}) {
+        if (g > maxg) break;
+        vx_trace_opts c = cur; c.sort_cell_log2 = g; consider(c);
+    }
+    for (int r : {1, 4, 16, 24, 32}) { vx_trace_opts c = cur; c.refill = r; consider(c); }
+    for (int bu : {1, 2, 8, 16, 64}) { vx_trace_opts c = cur; c.burst = bu; consider(c); }
+    for (int bl : {64, 128}) { vx_trace_opts c = cur; c.block = bl; consider(c); }
+    { vx_trace_opts c = cur; c.mode = VX_MODE_PLAIN; consider(c); }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(hits);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lock(V.tune_mu);
+        V.tuned_opts = cur;
+        V.tuned = true;
+    }
+    if (best_out) *best_out = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return VX_OK;
 }
 
 extern "C" int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,

@@ -62,8 +62,35 @@ const KernelSet* kernels_for(const Spec& sp) {
 
 int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
                  void* stream) {
+    // VX_MODE_AUTO takes the autotuned options when the volume has them.
+    vx_trace_opts tuned;
+    if (!o || o->mode == VX_MODE_AUTO) {
+        Volume& mv = const_cast<Volume&>(v);
+        std::lock_guard<std::mutex> lock(mv.tune_mu);
+        if (mv.tuned) {
+            tuned = mv.tuned_opts;
+            o = &tuned;
+        }
+    }
     const int block = pick_block(o);
     const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PERSISTENT;
+    const int sort = o ? o->sort_cell_log2 : 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    // Optional coherence sort: scratch from the stream-ordered pool, freed
+    // on the same stream after the trace.
+    void* scratch = nullptr;
+    uint32_t* order = nullptr;
+    if (sort > 0) {
+        const uint64_t bytes = sort_scratch_bytes(v.spec.ldim, sort, n, nullptr);
+        cudaError_t ce = cudaMallocAsync(&scratch, bytes, st);
+        if (ce) return fail(ce == cudaErrorMemoryAllocation ? VX_ENOMEM : VX_ECUDA, "sort scratch: %s",
+                            cudaGetErrorString(ce));
+        int rc = sort_rays(v.spec.ldim, sort, rays, n, scratch, &order, st);
+        if (rc) {
+            cudaFreeAsync(scratch, st);
+            return rc;
+        }
+    }
     int e;
     if (mode == VX_MODE_PERSISTENT) {
         unsigned long long* next = v.queue_counter();
@@ -71,12 +98,13 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
-        e = v.kernels->trace_persistent(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout,
-                                        block, bps, refill, burst, (cudaStream_t)stream, next);
+        e = v.kernels->trace_persistent(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), order, n, hits,
+                                        layout, block, bps, refill, burst, st, next);
     } else {
-        e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout, block,
-                             (cudaStream_t)stream);
+        e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
+                             block, st);
     }
+    if (scratch) cudaFreeAsync(scratch, st);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }

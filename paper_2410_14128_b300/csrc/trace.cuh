@@ -616,11 +616,15 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// `order` (optional): launch slot k traces ray order[k] and writes its hit
+// at order[k] (rays sorted for coherence, results in the caller's order).
 template <class F, int LAYOUT>
 __global__ void __launch_bounds__(256) k_trace(F f, const uint32_t* __restrict__ pool, const float4* __restrict__ rays,
-                                               uint64_t n, void* __restrict__ hits) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+                                               const uint32_t* __restrict__ order, uint64_t n,
+                                               void* __restrict__ hits) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint64_t i = order ? (uint64_t)__ldg(order + k) : k;
     const RayIn r = load_ray(rays, i);
     Cnt cnt;
     const HitRec h = trace_ray<false>(f, pool, r, cnt);
@@ -663,7 +667,8 @@ __global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __rest
 // `next` must be zero at launch; the kernel leaves it >= n.
 template <class F, int LAYOUT>
 __global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t* __restrict__ pool,
-                                                          const float4* __restrict__ rays, uint64_t n,
+                                                          const float4* __restrict__ rays,
+                                                          const uint32_t* __restrict__ order, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
                                                           int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
@@ -686,8 +691,9 @@ __global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t
             base = __shfl_sync(0xffffffffu, base, leader);
             if (base + (unsigned long long)__popc(idle) >= n) exhausted = true;
             if (!live) {
-                idx = base + __popc(idle & lt_mask);
-                if (idx < n) {
+                const uint64_t slot = base + __popc(idle & lt_mask);
+                if (slot < n) {
+                    idx = order ? (uint64_t)__ldg(order + slot) : slot;
                     HitRec h;
                     if (w.start(f, pool, load_ray(rays, idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
                     else live = true;
@@ -727,27 +733,27 @@ struct KernelSet {
     const char* spec;
     bool specialized;
     FmtParams params;
-    int (*trace)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits, int layout,
-                 int block, cudaStream_t st);
+    int (*trace)(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order, uint64_t n,
+                 void* hits, int layout, int block, cudaStream_t st);
     int (*render)(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
                        int layout, int block, cudaStream_t st, unsigned long long* counters);
-    int (*trace_persistent)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
-                            int layout, int block, int blocks_per_sm, int refill, int burst, cudaStream_t st,
-                            unsigned long long* next);
+    int (*trace_persistent)(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order,
+                            uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
+                            cudaStream_t st, unsigned long long* next);
 };
 
 template <class F>
 struct Launch {
     static F make(const FmtParams& p);
-    static int trace(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits, int layout,
-                     int block, cudaStream_t st) {
+    static int trace(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order, uint64_t n,
+                     void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0) k_trace<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
-        else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits);
+        if (layout == 0) k_trace<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
         return (int)cudaGetLastError();
     }
     static int trace_count(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
@@ -760,9 +766,9 @@ struct Launch {
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
-    static int trace_persistent(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
-                                int layout, int block, int blocks_per_sm, int refill, int burst, cudaStream_t st,
-                                unsigned long long* next) {
+    static int trace_persistent(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order,
+                                uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
+                                int burst, cudaStream_t st, unsigned long long* next) {
         if (n == 0) return 0;
         const F f = make(p);
         int dev = 0, sms = 0;
@@ -782,9 +788,11 @@ struct Launch {
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         if (layout == 0)
-            k_trace_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, next, refill, burst);
+            k_trace_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill,
+                                                                        burst);
         else
-            k_trace_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, next, refill, burst);
+            k_trace_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill,
+                                                                        burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,

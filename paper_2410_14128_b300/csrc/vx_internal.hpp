@@ -109,6 +109,9 @@ struct Volume {
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
     Staging staging;
+    std::mutex tune_mu;
+    bool tuned = false;
+    vx_trace_opts tuned_opts{};             // chosen by vx_autotune, used for VX_MODE_AUTO
     unsigned long long* d_queue = nullptr;  // kQueueRing counters
     mutable std::atomic<uint32_t> queue_slot{0};
     unsigned long long* queue_counter() const {
@@ -132,6 +135,9 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
+uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbins_out);
+int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* scratch, uint32_t** order_out,
+              struct CUstream_st* st);
 int trace_noalloc(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, void* stream);
 int camera_params(const vx_camera* cam, CameraParams* out);
 

@@ -281,3 +281,33 @@ def test_persistent_small_and_repeated():
         assert np.array_equal(vx.hits_to_numpy(h), ref)
     with pytest.raises(vx.VxError):
         gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, refill=33)
+
+
+# ---------------------------------------------------------------------------
+# Coherence sort: same hits, in the caller's order, for every granularity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "G(7)"])
+def test_sorted_trace_equals_unsorted(spec):
+    g = synth.terrain_volume(81, 128)
+    rays = np.concatenate([synth.incoherent_rays(82, 128, 50001), synth.box_rays(83, 128, 40, 20000),
+                           lattice_rays(84, (128, 128, 128), 3000)])
+    rays[5] = [np.nan, 1, 1, 0, 1, 0, 0, np.inf]  # invalid rays sort too
+    vol = vx.Volume(spec, g)
+    ref = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    compare(g, rays, ref)
+    for mode in (vx.MODE_PLAIN, vx.MODE_PERSISTENT):
+        for sort in (1, 3, 5, 7, 15):
+            got = gpu_trace(vol, rays, mode=mode, sort=sort)
+            assert np.array_equal(got, ref), (mode, sort)
+    with pytest.raises(vx.VxError):
+        gpu_trace(vol, rays, sort=16)
+
+
+def test_autotune_keeps_results():
+    g = synth.terrain_volume(85, 128)
+    rays = synth.incoherent_rays(86, 128, 200000)
+    vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
+    ref = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    best = vol.autotune(torch.from_numpy(rays[:100000]).cuda())
+    assert best["mode"] in ("plain", "persistent") and best["sample_ms"] > 0
+    assert np.array_equal(gpu_trace(vol, rays), ref)  # default mode now uses the tuned options
