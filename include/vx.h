@@ -233,6 +233,28 @@ int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hi
 int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
                      const vx_trace_opts* opts, void* stream, unsigned long long* counters);
 
+/* Several ray sets, possibly through different volumes (all on one device),
+ * in one call: the sets are grouped by format, each group (up to 64 sets) is
+ * traced by one persistent kernel whose warps take rays from a queue that
+ * spans all of the group's sets, and the groups' kernels run concurrently on
+ * forked streams, sharing the SMs in proportion to their rays.  Hits of set k
+ * land in items[k].hits in the set's own order, exactly as vx_trace would
+ * write them.  The call enqueues work on `stream` and returns; it allocates
+ * nothing and does not synchronise, so it can be captured into a CUDA graph
+ * (make one uncaptured call per device first: it creates the library's
+ * fork streams).  opts: mode/refill/burst/block as for vx_trace (NULL or
+ * VX_MODE_AUTO: the first volume's tuned options); sorting is not supported
+ * here (VX_EUNSUPPORTED).  Calls for one device are enqueued one at a time.
+ * (Not in the paper: it traces one frame of one format at a time.) */
+typedef struct vx_batch_item {
+    vx_volume volume;
+    const vx_ray* rays; /* device, 16-byte aligned */
+    uint64_t n;
+    void* hits;         /* device, per hit_layout */
+} vx_batch_item;
+int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
+                   void* stream);
+
 /* Picks vx_trace options for this volume: times candidates on `rays` (a
  * device sample of the rays the caller will trace, n of them) with CUDA
  * events on `stream` -- persistent refill threshold, iterations per refill

@@ -65,6 +65,11 @@ class _TraceOpts(ctypes.Structure):
                 ("sort_cell_log2", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_void_p), ("rays", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("hits", ctypes.c_void_p)]
+
+
 class _Camera(ctypes.Structure):
     _fields_ = [("eye", ctypes.c_double * 3), ("look", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
                 ("vfov_deg", ctypes.c_double), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32)]
@@ -85,6 +90,8 @@ _SIGS = {
                                 ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_trace_counted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p]),
+    "vx_trace_batch": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
+                                      ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                    ctypes.POINTER(_TraceOpts), ctypes.POINTER(ctypes.c_double)]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -310,6 +317,19 @@ class Volume:
         _check(lib().vx_render_host(self._h, ctypes.byref(c), ctypes.c_void_p(out.ctypes.data), layout,
                                     ctypes.byref(o), _stream_handle(stream)))
         return out
+
+
+def trace_batch(items, layout: int = HIT_FULL, stream=None, **opts):
+    """items: list of (Volume, rays tensor, hits tensor); one vx_trace_batch call."""
+    arr = (_BatchItem * max(1, len(items)))()
+    for k, (vol, rays, hits) in enumerate(items):
+        arr[k].volume = vol.handle
+        arr[k].rays = rays.data_ptr()
+        arr[k].n = rays.shape[0]
+        arr[k].hits = hits.data_ptr()
+    o = _opts(**opts) if opts else None
+    _check(lib().vx_trace_batch(arr, len(items), layout, ctypes.byref(o) if o is not None else None,
+                                _stream_handle(stream)))
 
 
 def raygen_pinhole(cam: dict, rays=None, stream=None):

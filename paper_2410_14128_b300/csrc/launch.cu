@@ -16,8 +16,15 @@ std::vector<const KernelSet*>& registry() {
     static std::vector<const KernelSet*> r;
     return r;
 }
-const KernelSet g_generic = {"*", false, FmtParams{}, &Launch<DynF>::trace, &Launch<DynF>::render,
-                             &Launch<DynF>::trace_count, &Launch<DynF>::trace_persistent};
+const KernelSet g_generic = {"*",
+                             false,
+                             FmtParams{},
+                             &Launch<DynF>::trace,
+                             &Launch<DynF>::render,
+                             &Launch<DynF>::trace_count,
+                             &Launch<DynF>::trace_persistent,
+                             &Launch<DynF>::trace_batch,
+                             &Launch<DynF>::resident_blocks};
 
 CamDev to_dev(const CameraParams& c) {
     CamDev d;
@@ -123,6 +130,111 @@ int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t
     const int block = pick_block(o);
     int e = v.kernels->render(v.spec.fmt, v.d_pool, to_dev(cp), i0, n, hits, layout, block, (cudaStream_t)stream);
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    return VX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched tracing: group the sets by format, one persistent launch per group
+// (sub-groups of kBatchMax sets), all launches concurrent on forked streams,
+// the SMs shared in proportion to each launch's rays.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kForkStreams = 8;
+struct DevStreams {
+    bool ready = false;
+    cudaStream_t s[kForkStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kForkStreams];
+};
+std::mutex g_fork_mu;
+DevStreams g_fork[64];
+}  // namespace
+
+int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64) return fail(VX_EUNSUPPORTED, "device %d", dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // group by (kernel set, format parameters)
+    struct Sub {
+        const KernelSet* ks;
+        const Volume* v0;
+        BatchDesc d;
+    };
+    std::vector<Sub> subs;
+    uint64_t total = 0;
+    for (const BatchItemIn& it : items) {
+        if (it.n == 0) continue;
+        total += it.n;
+        Sub* g = nullptr;
+        for (Sub& s2 : subs)
+            if (s2.ks == it.v->kernels && same_params(s2.v0->spec.fmt, it.v->spec.fmt) && s2.d.count < kBatchMax) {
+                g = &s2;
+                break;
+            }
+        if (!g) {
+            subs.push_back(Sub{it.v->kernels, it.v, BatchDesc{}});
+            g = &subs.back();
+            g->d.count = 0;
+            g->d.start[0] = 0;
+        }
+        const uint32_t k = g->d.count++;
+        g->d.pool[k] = it.v->d_pool;
+        g->d.rays[k] = reinterpret_cast<const float4*>(it.rays);
+        g->d.hits[k] = it.hits;
+        g->d.start[k + 1] = g->d.start[k] + it.n;
+    }
+    if (subs.empty()) return VX_OK;
+    vx_trace_opts def{};
+    if (!o || o->mode == VX_MODE_AUTO) {
+        Volume& mv = const_cast<Volume&>(*subs[0].v0);
+        std::lock_guard<std::mutex> lock(mv.tune_mu);
+        def = mv.tuned ? mv.tuned_opts : vx_trace_opts{};
+    } else {
+        def = *o;
+    }
+    const int block = def.block > 0 ? def.block : 256;
+    const int refill = def.refill > 0 ? def.refill : kDefaultRefill;
+    const int burst = def.burst > 0 ? def.burst : kDefaultBurst;
+
+    std::lock_guard<std::mutex> lock(g_fork_mu);
+    DevStreams& F = g_fork[dev];
+    if (!F.ready) {
+        for (int i = 0; i < kForkStreams; i++) {
+            cudaError_t e = cudaStreamCreateWithFlags(&F.s[i], cudaStreamNonBlocking);
+            if (!e) e = cudaEventCreateWithFlags(&F.join[i], cudaEventDisableTiming);
+            if (e) return fail(VX_ECUDA, "batch streams: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = cudaEventCreateWithFlags(&F.fork, cudaEventDisableTiming);
+        if (e) return fail(VX_ECUDA, "batch events: %s", cudaGetErrorString(e));
+        F.ready = true;
+    }
+    cudaError_t e = cudaEventRecord(F.fork, st);
+    if (e) return fail(VX_ECUDA, "batch fork: %s", cudaGetErrorString(e));
+    const int nsub = (int)subs.size();
+    for (int i = 0; i < nsub && i < kForkStreams; i++) cudaStreamWaitEvent(F.s[i], F.fork, 0);
+    for (int i = 0; i < nsub; i++) {
+        Sub& g = subs[i];
+        int per_sm = 1;
+        int rc = g.ks->resident_blocks(layout, block, &per_sm);
+        if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
+        const uint64_t n = g.d.start[g.d.count];
+        uint64_t grid = (uint64_t)((double)sms * per_sm * (double)n / (double)total + 0.999);
+        const uint64_t need = (n + block - 1) / block;
+        if (grid > need) grid = need;
+        if (grid < 1) grid = 1;
+        unsigned long long* next = g.v0->queue_counter();
+        rc = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, (int)grid, refill, burst, F.s[i % kForkStreams],
+                               next);
+        if (rc) return fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)rc));
+    }
+    for (int i = 0; i < nsub && i < kForkStreams; i++) {
+        cudaEventRecord(F.join[i], F.s[i]);
+        cudaStreamWaitEvent(st, F.join[i], 0);
+    }
+    e = cudaGetLastError();
+    if (e) return fail(VX_ECUDA, "batch: %s", cudaGetErrorString(e));
     return VX_OK;
 }
 

@@ -714,6 +714,79 @@ __global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t
     }
 }
 
+// Batched variant: the ray sets of several volumes with the same format in
+// one persistent launch.  The descriptor travels in the kernel parameters;
+// the queue spans the concatenated sets (set k owns slots start[k] ..
+// start[k+1]-1), so warps move from set to set as sets run dry.
+constexpr int kBatchMax = 64;
+struct BatchDesc {
+    uint32_t count;
+    const uint32_t* pool[kBatchMax];
+    const float4* rays[kBatchMax];
+    void* hits[kBatchMax];
+    uint64_t start[kBatchMax + 1];
+};
+
+template <class F, int LAYOUT>
+__global__ void __launch_bounds__(256, 3) k_trace_batch(F f, const __grid_constant__ BatchDesc desc,
+                                                     unsigned long long* next, int refill, int burst) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t n = desc.start[desc.count];
+    uint32_t P[F::kMaxJ], M[F::kMaxJ];
+    Walker<false, F> w;
+    w.P = P;
+    w.M = M;
+    bool live = false;
+    bool exhausted = false;  // warp-uniform
+    uint64_t idx = 0;
+    int set = 0;
+    const uint32_t* pool = nullptr;
+    void* hits = nullptr;
+    while (true) {
+        const unsigned idle = __ballot_sync(0xffffffffu, !live);
+        if (exhausted) {
+            if (idle == 0xffffffffu) break;
+        } else if (__popc(idle) >= refill) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(next, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (base + (unsigned long long)__popc(idle) >= n) exhausted = true;
+            if (!live) {
+                const uint64_t slot = base + __popc(idle & lt_mask);
+                if (slot < n) {
+                    // the set holding this slot (binary search over the prefix)
+                    int lo = 0, hi = (int)desc.count - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (desc.start[mid] <= slot) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    set = lo;
+                    idx = slot - desc.start[set];
+                    pool = desc.pool[set];
+                    hits = desc.hits[set];
+                    HitRec h;
+                    if (w.start(f, pool, load_ray(desc.rays[set], idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
+                    else live = true;
+                }
+            }
+            continue;
+        }
+        if (live) {
+            for (int k = 0; k < burst; k++) {
+                HitRec h;
+                if (w.step(f, pool, h)) {
+                    store_hit<LAYOUT>(f, hits, idx, h);
+                    live = false;
+                    break;
+                }
+            }
+        }
+    }
+}
+
 template <class F, int LAYOUT>
 __global__ void __launch_bounds__(256) k_render(F f, const uint32_t* __restrict__ pool, CamDev cam, uint64_t i0,
                                                 uint64_t n, void* __restrict__ hits) {
@@ -742,6 +815,10 @@ struct KernelSet {
     int (*trace_persistent)(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
                             cudaStream_t st, unsigned long long* next);
+    // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
+    int (*trace_batch)(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill, int burst,
+                       cudaStream_t st, unsigned long long* next);
+    int (*resident_blocks)(int layout, int block, int* per_sm);
 };
 
 template <class F>
@@ -795,6 +872,22 @@ struct Launch {
                                                                         burst);
         return (int)cudaGetLastError();
     }
+    static int resident_blocks(int layout, int block, int* per_sm) {
+        cudaError_t e = layout == 0
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, 0);
+        if (*per_sm < 1) *per_sm = 1;
+        return (int)e;
+    }
+    static int trace_batch(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill,
+                           int burst, cudaStream_t st, unsigned long long* next) {
+        const F f = make(p);
+        cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+        if (e) return (int)e;
+        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
+        else k_trace_batch<F, 1><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
+        return (int)cudaGetLastError();
+    }
     static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,
                       void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
@@ -821,7 +914,7 @@ template <class Fm>
 KernelSet make_kernel_set(const char* spec) {
     using F = typename Fm::F;
     return KernelSet{spec, true, Fm::P, &Launch<F>::trace, &Launch<F>::render, &Launch<F>::trace_count,
-                     &Launch<F>::trace_persistent};
+                     &Launch<F>::trace_persistent, &Launch<F>::trace_batch, &Launch<F>::resident_blocks};
 }
 
 void register_kernel_set(const KernelSet* ks);

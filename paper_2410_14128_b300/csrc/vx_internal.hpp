@@ -135,6 +135,13 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
+struct BatchItemIn {
+    const Volume* v;
+    const vx_ray* rays;
+    uint64_t n;
+    void* hits;
+};
+int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream);
 uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbins_out);
 int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* scratch, uint32_t** order_out,
               struct CUstream_st* st);

@@ -311,3 +311,63 @@ def test_autotune_keeps_results():
     best = vol.autotune(torch.from_numpy(rays[:100000]).cuda())
     assert best["mode"] in ("plain", "persistent") and best["sample_ms"] > 0
     assert np.array_equal(gpu_trace(vol, rays), ref)  # default mode now uses the tuned options
+
+
+# ---------------------------------------------------------------------------
+# Batched tracing: many sets over several volumes in one call (and a graph)
+# ---------------------------------------------------------------------------
+def _batch_setup(seed, n_sets):
+    g1 = synth.terrain_volume(seed, 128)
+    g2 = synth.random_grid(seed + 1, (64, 64, 64), 0.05)
+    vols = [vx.Volume("R(3,3,3) S(2) G(2)", g1), vx.Volume("R(2,2,2) R(2,2,2) R(3,3,3)", g1),
+            vx.Volume("G(6)", g2), vx.Volume("R(1,1,1) S(2) G(3)", g2)]  # last: run-time-described format
+    grids = [g1, g1, g2, g2]
+    rng = np.random.default_rng(seed)
+    sets = []
+    for k in range(n_sets):
+        v = k % len(vols)
+        n = int(rng.choice([0, 1, 31, 1000, 17000, 70000]))
+        side = grids[v].shape[0]
+        if k % 2:
+            rays = synth.incoherent_rays(seed + 10 + k, side, max(n, 1))[:n]
+        else:
+            rays = synth.aimed_rays(seed + 10 + k, (side, side, side), max(n, 1))[:n]
+        sets.append((v, np.ascontiguousarray(rays)))
+    return vols, grids, sets
+
+
+def test_batch_equals_per_set_trace():
+    vols, grids, sets = _batch_setup(101, 150)  # > 64 sets per format: split launches
+    dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
+    vx.trace_batch([(vols[v], r, h) for v, r, h in dev])
+    torch.cuda.synchronize()
+    for (v, r_np), (_, r, h) in zip(sets, dev):
+        if len(r_np) == 0:
+            continue
+        ref = gpu_trace(vols[v], r_np, mode=vx.MODE_PLAIN)
+        assert np.array_equal(vx.hits_to_numpy(h), ref)
+    # spot-check against the oracle
+    for (v, r_np), (_, r, h) in list(zip(sets, dev))[:8]:
+        if len(r_np):
+            compare(grids[v], r_np, vx.hits_to_numpy(h))
+
+
+def test_batch_in_cuda_graph():
+    vols, grids, sets = _batch_setup(202, 24)
+    dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
+    items = [(vols[v], r, h) for v, r, h in dev]
+    vx.trace_batch(items)  # first call outside capture creates the fork streams
+    torch.cuda.synchronize()
+    for _, _, h in dev:
+        h.fill_(0)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        vx.trace_batch(items)
+    for rep in range(3):
+        for _, _, h in dev:
+            h.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        for (v, r_np), (_, r, h) in zip(sets, dev):
+            if len(r_np):
+                assert np.array_equal(vx.hits_to_numpy(h), gpu_trace(vols[v], r_np, mode=vx.MODE_PLAIN)), rep
