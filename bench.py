@@ -147,7 +147,7 @@ def oracle_rate(grid, cam, inc, budget_s: float, threads: int | None = None):
     rng = np.random.default_rng(5)
     pi = rng.permutation(len(prim))
     ii = rng.permutation(len(inc))
-    chunk = 20000
+    chunk = max(20000, 2048 * (os.cpu_count() or 1))
     done, t_used, used_threads, k = 0, 0.0, 1, 0
     while t_used < budget_s and (k + 1) * chunk <= min(len(prim), len(inc)):
         sample = np.concatenate([prim[pi[k * chunk:(k + 1) * chunk]], inc[ii[k * chunk:(k + 1) * chunk]]])

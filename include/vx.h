@@ -95,9 +95,11 @@ typedef struct vx_hit_compact {
 typedef struct vx_volume_s* vx_volume;
 
 /* Source grid of a build, the role of the paper's voxelizer (Sec. 4.1,
- * Sec. 5).  Exactly one of `dense` and `fill_brick` is set.
+ * Sec. 5).  Exactly one of `dense`, `dense_pal` and `fill_brick` is set.
  *   log2_dim  grid size per axis, 2^log2_dim[i] voxels (<= 2^15);
  *   dense     host array of 2^(sum log2_dim) RGBA words, x fastest;
+ *   dense_pal host array of 2^(sum log2_dim) 8-bit palette indices, x
+ *             fastest, with `palette` (256 RGBA words, palette[0] = 0);
  *   fill_brick  called with a cube of side 2^log2_size whose corner
  *             (x0,y0,z0) is a multiple of its side; writes the cube's words,
  *             x fastest, to `out`; returns 0 on success;
@@ -113,6 +115,8 @@ typedef struct vx_grid {
     vx_fill_brick_fn fill_brick;
     vx_block_empty_fn block_empty;
     void* user;
+    const uint8_t* dense_pal;
+    const uint32_t* palette;
 } vx_grid;
 
 #define VX_DEDUP_PER_SUBVOLUME 0
@@ -309,6 +313,20 @@ typedef struct vx_camera {
 
 /* Writes width*height rays to `rays` (device, 16-byte aligned). */
 int vx_raygen_pinhole(const vx_camera* cam, vx_ray* rays, void* stream);
+
+/* Ambient-occlusion rays from n primary rays and their full hit records
+ * (device): spp rays per primary, index i * spp + k, cosine-weighted about
+ * the outward normal of the face the primary ray entered (Malley's method:
+ * uniform point on the unit disk, r = sqrt(u1), phi = 2 pi u2, lifted by
+ * z = sqrt(1 - u1)); tangents e_{a+1}, e_{a+2} (mod 3) for normal axis a.
+ * u1, u2 = top 24 bits of SplitMix64(SplitMix64(seed) ^ c), c = (i * spp +
+ * k) * 2 and c + 1 (Steele, Lea & Flood 2014).  Origin = o + t d of the
+ * primary, moved eps along the normal; tmin 0, tmax `tmax`.  Misses and
+ * hits with face 0 give the all-zero ray (traced as a miss).  The paper
+ * evaluates without shading from bounces (Fig. 5 caption); this is the
+ * secondary-ray workload of the benchmark. */
+int vx_raygen_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, uint32_t spp, float eps, float tmax,
+                 vx_ray* out, void* stream);
 
 /* Pinhole rays generated and traced in one kernel (no ray array in memory);
  * hits as for vx_trace, one per pixel. */

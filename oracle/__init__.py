@@ -72,6 +72,7 @@ def lib():
         L.or_decode.argtypes = [vp, ctypes.c_uint64, ctypes.c_char_p, vp, i64, i64, i64]
         L.or_spec_dims.argtypes = [ctypes.c_char_p, vp]
         L.or_sizeof.argtypes = [i32]
+        L.or_ao_rays.argtypes = [vp, vp, i64, ctypes.c_uint64, i32, dbl, dbl, vp]
         for name, dt in (("hit", HIT_DTYPE), ("tie", TIE_DTYPE), ("bf", BF_DTYPE)):
             which = {"hit": 0, "tie": 1, "bf": 2}[name]
             if L.or_sizeof(which) != dt.itemsize:
@@ -174,3 +175,26 @@ def decode(words: np.ndarray, spec: str) -> np.ndarray:
 def lin(x, y, z, dims):
     nx, ny, _ = dims
     return x + nx * (y + ny * z)
+
+
+def ao_rays(rays: np.ndarray, hits, seed: int, spp: int = 8, eps: float = 1e-3, tmax: float = 32.0) -> np.ndarray:
+    """FP64 ambient-occlusion rays (cosine-weighted, Malley) from primary
+    rays and their oracle hits: (n * spp, 8) float32; see oracle.c."""
+    r = _rays(rays)
+    h = np.ascontiguousarray(hits, dtype=HIT_DTYPE)
+    out = np.empty((r.shape[0] * spp, 8), dtype=np.float32)
+    lib().or_ao_rays(_p(r), _p(h), r.shape[0], seed, spp, eps, tmax, _p(out))
+    return out
+
+
+def classify_pal(grid8: np.ndarray, palette: np.ndarray, rays: np.ndarray, eps_rel: float = EPS_REL,
+                 threads: int | None = None):
+    """Same as :func:`classify` for a uint8 palette-index grid."""
+    L = lib()
+    g = np.ascontiguousarray(grid8, dtype=np.uint8)
+    pal = np.ascontiguousarray(palette, dtype=np.uint32)
+    nz, ny, nx = g.shape
+    r = _rays(rays)
+    out = np.zeros(r.shape[0], dtype=TIE_DTYPE)
+    L.or_classify_pal(_p(g), _p(pal), nx, ny, nz, _p(r), r.shape[0], eps_rel, _p(out), threads or default_threads())
+    return out

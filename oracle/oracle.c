@@ -767,3 +767,61 @@ int or_sizeof(int which) {
         default: return -1;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Ambient-occlusion rays (FP64, rounded once to float32).                   */
+/* For primary ray i with a hit on face f (1 + 2a + s, a = axis, s = 1 when  */
+/* the ray moved towards -a): the outward normal of the entered face is     */
+/* n = -e_a (s = 0) or +e_a (s = 1); sample k of spp draws two uniforms      */
+/* u1, u2 from SplitMix64 (Steele, Lea & Flood 2014) of the counter          */
+/* c = (i * spp + k) * 2 + {0, 1} mixed with the seed, keeping the top 24    */
+/* bits; Malley's method: a uniform point on the unit disk, r = sqrt(u1),    */
+/* phi = 2 pi u2, lifted to the hemisphere, z = sqrt(1 - u1): a cosine-      */
+/* weighted direction d = r cos(phi) e_{a+1} + r sin(phi) e_{a+2} + z n      */
+/* (axes mod 3).  Origin: the hit point o + t d_primary moved eps along n;   */
+/* tmin 0, tmax = tmax_ao.  Misses and face-0 hits give the empty ray        */
+/* {0,0,0, 0, 0,0,0, 0}.  Output ray i * spp + k.                            */
+/* ------------------------------------------------------------------------ */
+static uint64_t ao_mix(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+static double ao_u24(uint64_t seed, uint64_t c) {
+    uint64_t h = ao_mix(ao_mix(seed) ^ c);
+    return (double)(h >> 40) / 16777216.0;
+}
+
+void or_ao_rays(const float* rays, const or_hit* hits, int64_t n, uint64_t seed, int spp, double eps, double tmax_ao,
+                float* out) {
+    const double PI = 3.14159265358979323846264338327950288;
+    for (int64_t i = 0; i < n; i++) {
+        const or_hit* h = &hits[i];
+        for (int k = 0; k < spp; k++) {
+            float* o = out + 8 * (i * spp + k);
+            if (h->status != ST_HIT || h->face == 0) {
+                for (int q = 0; q < 8; q++) o[q] = 0.0f;
+                continue;
+            }
+            const int a = (h->face - 1) / 2, s = (h->face - 1) & 1;
+            const double sign = s ? 1.0 : -1.0;
+            const uint64_t c = ((uint64_t)i * (uint64_t)spp + (uint64_t)k) * 2u;
+            const double u1 = ao_u24(seed, c), u2 = ao_u24(seed, c + 1);
+            const double r = sqrt(u1), phi = 2.0 * PI * u2;
+            const double lx = r * cos(phi), ly = r * sin(phi), lz = sqrt(1.0 - u1 > 0.0 ? 1.0 - u1 : 0.0);
+            double d[3] = {0, 0, 0}, p[3];
+            d[(a + 1) % 3] = lx;
+            d[(a + 2) % 3] = ly;
+            d[a] = sign * lz;
+            const float* pr = rays + 8 * i;
+            for (int q = 0; q < 3; q++) p[q] = (double)pr[q] + h->t * (double)pr[4 + q];
+            p[a] += sign * eps;
+            o[0] = (float)p[0]; o[1] = (float)p[1]; o[2] = (float)p[2];
+            o[3] = 0.0f;
+            o[4] = (float)d[0]; o[5] = (float)d[1]; o[6] = (float)d[2];
+            o[7] = (float)tmax_ao;
+        }
+    }
+}

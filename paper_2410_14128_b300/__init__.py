@@ -43,7 +43,8 @@ BLOCK_EMPTY = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, c
 
 class _Grid(ctypes.Structure):
     _fields_ = [("log2_dim", ctypes.c_uint32 * 3), ("dense", ctypes.c_void_p), ("fill_brick", FILL_BRICK),
-                ("block_empty", BLOCK_EMPTY), ("user", ctypes.c_void_p)]
+                ("block_empty", BLOCK_EMPTY), ("user", ctypes.c_void_p), ("dense_pal", ctypes.c_void_p),
+                ("palette", ctypes.c_void_p)]
 
 
 class _BuildOpts(ctypes.Structure):
@@ -99,6 +100,9 @@ _SIGS = {
     "vx_trace_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p]),
     "vx_raygen_pinhole": (ctypes.c_int, [ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_void_p]),
+    "vx_raygen_ao": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_uint32, ctypes.c_float, ctypes.c_float, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "vx_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_render_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
@@ -178,12 +182,28 @@ def hits_to_numpy(hits, layout: int = HIT_FULL) -> np.ndarray:
 class Volume:
     """A hybrid-format volume: built on the host, resident on one GPU."""
 
-    def __init__(self, spec: str, grid: np.ndarray | None = None, *, log2_dim=None, fill_brick=None,
-                 block_empty=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1, upload: bool = True):
+    def __init__(self, spec: str, grid: np.ndarray | None = None, *, palette=None, log2_dim=None,
+                 fill_brick=None, block_empty=None, user=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1,
+                 upload: bool = True):
+        """grid: dense (nz, ny, nx) uint32 RGBA array, or uint8 palette
+        indices with `palette` (256 words); or log2_dim + fill_brick (a Python
+        callable, or the address of a C function with the vx_fill_brick_fn
+        signature) with optional block_empty and user."""
         L = lib()
         g = _Grid()
         self._keep = []
-        if grid is not None:
+        if grid is not None and palette is not None:
+            arr = np.ascontiguousarray(grid, dtype=np.uint8)
+            pal = np.ascontiguousarray(palette, dtype=np.uint32)
+            assert pal.shape == (256,)
+            nz, ny, nx = arr.shape
+            dims = [n.bit_length() - 1 for n in (nx, ny, nz)]
+            if any(n & (n - 1) for n in (nx, ny, nz)):
+                raise ValueError("grid sides must be powers of two")
+            self._keep += [arr, pal]
+            g.dense_pal = arr.ctypes.data
+            g.palette = pal.ctypes.data
+        elif grid is not None:
             arr = np.ascontiguousarray(grid, dtype=np.uint32)
             nz, ny, nx = arr.shape
             dims = []
@@ -204,6 +224,8 @@ class Volume:
                 be = BLOCK_EMPTY(block_empty)
                 self._keep.append(be)
                 g.block_empty = be
+            if user is not None:
+                g.user = user.value if isinstance(user, ctypes.c_void_p) else user
         for i in range(3):
             g.log2_dim[i] = dims[i]
         o = _BuildOpts(dedup, device, 0 if upload else 1, 0)
@@ -330,6 +352,17 @@ def trace_batch(items, layout: int = HIT_FULL, stream=None, **opts):
     o = _opts(**opts) if opts else None
     _check(lib().vx_trace_batch(arr, len(items), layout, ctypes.byref(o) if o is not None else None,
                                 _stream_handle(stream)))
+
+
+def raygen_ao(rays, hits, seed: int, spp: int = 8, eps: float = 1e-3, tmax: float = 32.0, out=None, stream=None):
+    """AO rays on the GPU from primary rays and full hit records."""
+    import torch
+    n = rays.shape[0]
+    if out is None:
+        out = torch.empty((n * spp, 8), dtype=torch.float32, device="cuda")
+    _check(lib().vx_raygen_ao(ctypes.c_void_p(rays.data_ptr()), ctypes.c_void_p(hits.data_ptr()), n, seed, spp, eps,
+                              tmax, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def raygen_pinhole(cam: dict, rays=None, stream=None):

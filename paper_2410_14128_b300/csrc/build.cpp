@@ -44,7 +44,9 @@ namespace {
 
 class DenseSource final : public VoxelSource {
   public:
-    DenseSource(const uint32_t* w, const int ld[3]) : w_(w) {
+    // Either RGBA words (w) or 8-bit palette indices (w8 + palette).
+    DenseSource(const uint32_t* w, const uint8_t* w8, const uint32_t* pal, const int ld[3])
+        : w_(w), w8_(w8), pal_(pal) {
         for (int i = 0; i < 3; i++) { ld_[i] = ld[i]; n_[i] = (int64_t)1 << ld[i]; }
         levels_ = std::max(ld[0], std::max(ld[1], ld[2])) + 1;
         pyr_.resize(levels_);
@@ -53,13 +55,37 @@ class DenseSource final : public VoxelSource {
             pyr_[m].assign((size_t)((pn_[m][0] * pn_[m][1] * pn_[m][2] + 63) / 64), 0ull);
         }
         const int64_t total = n_[0] * n_[1] * n_[2];
-        for (int64_t i = 0; i < total; i++)
-            if (w_[i]) pyr_[0][(size_t)(i >> 6)] |= 1ull << (i & 63);
-        for (int m = 1; m < levels_; m++)
-            for (int64_t z = 0; z < pn_[m - 1][2]; z++)
-                for (int64_t y = 0; y < pn_[m - 1][1]; y++)
-                    for (int64_t x = 0; x < pn_[m - 1][0]; x++)
-                        if (bit(m - 1, x, y, z)) set(m, x >> 1, y >> 1, z >> 1);
+        const int64_t words = (total + 63) / 64;
+        // level 0: one bit per voxel, 64 voxels per word (parallel over words)
+#pragma omp parallel for schedule(static)
+        for (int64_t wi = 0; wi < words; wi++) {
+            uint64_t bits = 0;
+            const int64_t i0 = wi * 64, i1 = std::min<int64_t>(i0 + 64, total);
+            for (int64_t i = i0; i < i1; i++)
+                if (w_ ? w_[i] != 0 : pal_[w8_[i]] != 0) bits |= 1ull << (i - i0);
+            pyr_[0][(size_t)wi] = bits;
+        }
+        // coarser levels: OR of 2x2x2 children (parallel over output z-slabs
+        // of 32 cells; each output word belongs to one slab when x-rows are
+        // a multiple of 64 cells, else serial)
+        for (int m = 1; m < levels_; m++) {
+            const int64_t X = pn_[m][0], Y = pn_[m][1], Z = pn_[m][2];
+            const bool par = (X * Y) % 64 == 0;
+#pragma omp parallel for schedule(static) if (par)
+            for (int64_t z = 0; z < Z; z++)
+                for (int64_t y = 0; y < Y; y++)
+                    for (int64_t x = 0; x < X; x++) {
+                        bool any = false;
+                        for (int dz = 0; dz < 2 && !any; dz++)
+                            for (int dy = 0; dy < 2 && !any; dy++)
+                                for (int dx = 0; dx < 2 && !any; dx++) {
+                                    const int64_t cx = 2 * x + dx, cy = 2 * y + dy, cz = 2 * z + dz;
+                                    if (cx < pn_[m - 1][0] && cy < pn_[m - 1][1] && cz < pn_[m - 1][2])
+                                        any = bit(m - 1, cx, cy, cz);
+                                }
+                        if (any) set(m, x, y, z);
+                    }
+        }
     }
     bool empty(int64_t x0, int64_t y0, int64_t z0, int s) override {
         if (s >= levels_) s = levels_ - 1;
@@ -68,9 +94,13 @@ class DenseSource final : public VoxelSource {
     int block(int64_t x0, int64_t y0, int64_t z0, int s, uint32_t* out) override {
         const int64_t side = (int64_t)1 << s;
         for (int64_t z = 0; z < side; z++)
-            for (int64_t y = 0; y < side; y++)
-                memcpy(out + side * (y + side * z), w_ + x0 + n_[0] * ((y0 + y) + n_[1] * (z0 + z)),
-                       sizeof(uint32_t) * side);
+            for (int64_t y = 0; y < side; y++) {
+                const int64_t row = x0 + n_[0] * ((y0 + y) + n_[1] * (z0 + z));
+                uint32_t* o = out + side * (y + side * z);
+                if (w_) memcpy(o, w_ + row, sizeof(uint32_t) * side);
+                else
+                    for (int64_t x = 0; x < side; x++) o[x] = pal_[w8_[row + x]];
+            }
         return 0;
     }
 
@@ -84,6 +114,8 @@ class DenseSource final : public VoxelSource {
         pyr_[m][(size_t)(i >> 6)] |= 1ull << (i & 63);
     }
     const uint32_t* w_;
+    const uint8_t* w8_;
+    const uint32_t* pal_;
     int ld_[3];
     int64_t n_[3];
     int levels_;
@@ -118,13 +150,11 @@ class BrickSource final : public VoxelSource {
         if (brick_empty(x0 >> bl_, y0 >> bl_, z0 >> bl_)) return true;
         const Brick* b = fetch(x0 >> bl_, y0 >> bl_, z0 >> bl_);
         if (!b) return false;
-        const int64_t side = (int64_t)1 << s, bs = (int64_t)1 << bl_;
-        const int64_t ox = x0 & (bs - 1), oy = y0 & (bs - 1), oz = z0 & (bs - 1);
-        for (int64_t z = 0; z < side; z++)
-            for (int64_t y = 0; y < side; y++)
-                for (int64_t x = 0; x < side; x++)
-                    if (b->w[(size_t)((ox + x) + bs * ((oy + y) + bs * (oz + z)))]) return false;
-        return true;
+        // the brick's occupancy pyramid: level s has (2^bl / 2^s)^3 cells
+        const int64_t bs = (int64_t)1 << bl_;
+        const int64_t m = bs >> s;
+        const int64_t i = ((x0 & (bs - 1)) >> s) + m * (((y0 & (bs - 1)) >> s) + m * ((z0 & (bs - 1)) >> s));
+        return !((b->pyr[s][(size_t)(i >> 6)] >> (i & 63)) & 1ull);
     }
     int block(int64_t x0, int64_t y0, int64_t z0, int s, uint32_t* out) override {
         const int64_t side = (int64_t)1 << s;
@@ -159,8 +189,30 @@ class BrickSource final : public VoxelSource {
     struct Brick {
         int64_t key;
         std::vector<uint32_t> w;
+        std::vector<uint64_t> pyr[7];  // occupancy bits per level (cells of side 2^level)
         uint64_t stamp;
     };
+    void build_pyramid(Brick& b) {
+        const int64_t bs = (int64_t)1 << bl_;
+        for (int l = 0; l <= bl_; l++) {
+            const int64_t m = bs >> l;
+            b.pyr[l].assign((size_t)((m * m * m + 63) / 64), 0ull);
+        }
+        for (int64_t i = 0; i < bs * bs * bs; i++)
+            if (b.w[(size_t)i]) b.pyr[0][(size_t)(i >> 6)] |= 1ull << (i & 63);
+        for (int l = 1; l <= bl_; l++) {
+            const int64_t mp = bs >> (l - 1), m = bs >> l;
+            for (int64_t z = 0; z < mp; z++)
+                for (int64_t y = 0; y < mp; y++)
+                    for (int64_t x = 0; x < mp; x++) {
+                        const int64_t i = x + mp * (y + mp * z);
+                        if ((b.pyr[l - 1][(size_t)(i >> 6)] >> (i & 63)) & 1ull) {
+                            const int64_t j = (x >> 1) + m * ((y >> 1) + m * (z >> 1));
+                            b.pyr[l][(size_t)(j >> 6)] |= 1ull << (j & 63);
+                        }
+                    }
+        }
+    }
     bool brick_empty(int64_t bx, int64_t by, int64_t bz) {
         size_t i = (size_t)(bx + nb_[0] * (by + nb_[1] * bz));
         if (!known_[i]) fetch(bx, by, bz);
@@ -187,9 +239,8 @@ class BrickSource final : public VoxelSource {
             err_ = VX_EINVAL;
             std::fill(slot->w.begin(), slot->w.end(), 0u);
         }
-        bool any = false;
-        for (uint32_t v : slot->w)
-            if (v) { any = true; break; }
+        build_pyramid(*slot);
+        const bool any = (slot->pyr[bl_][0] & 1ull) != 0;
         known_[(size_t)key] = any ? 2 : 1;
         return slot;
     }
@@ -239,6 +290,8 @@ class Builder {
             acc += sp.lv[k].e[0];
         }
         maps_.resize(nlev_);
+        leaf_cache_.assign(nlev_, std::vector<LeafSlot>(1u << kLeafCacheBits));
+        map_gen_.assign(nlev_, 1u);
         for (int i = 0; i < 3; i++) cb_[i] = std::min(5, sp.ldim[i]);
         cside_ = std::min(cb_[0], std::min(cb_[1], cb_[2]));
         cache_.resize((size_t)1 << (3 * cside_));
@@ -311,7 +364,10 @@ class Builder {
             if (any) R_.level_nodes[k]++;
             return any && !err_;
         }
-        if (L.kind == K_DAG && scope_ == VX_DEDUP_PER_SUBVOLUME) maps_[k].clear();
+        if (L.kind == K_DAG && scope_ == VX_DEDUP_PER_SUBVOLUME) {
+            maps_[k].clear();
+            map_gen_[k]++;  // invalidates the leaf cache of this level
+        }
         NodeKey root;
         bool ok = (L.kind == K_SVO) ? svo_node(k, lo, 0, root) : dag_node(k, lo, 0, root);
         if (!ok || err_) return false;
@@ -374,8 +430,31 @@ class Builder {
         auto& map = maps_[k];
         for (int i = 0; i < 8; i++) {
             if (!((valid >> i) & 1u)) continue;
-            auto it = map.find(ch[i]);
             uint32_t p;
+            // one-word leaf nodes repeat a few colours: a direct-mapped cache
+            // in front of the map (same results, fewer hash-map probes)
+            if (ch[i].n == 1) {
+                LeafSlot& ls = leaf_cache_[k][(ch[i].w[0] * 2654435761u) >> (32 - kLeafCacheBits)];
+                if (ls.gen == map_gen_[k] && ls.valid && ls.term == ch[i].w[0]) {
+                    out.w[out.n++] = ls.ptr;
+                    continue;
+                }
+                auto it = map.find(ch[i]);
+                if (it != map.end()) {
+                    p = it->second;
+                } else {
+                    p = write(k, ch[i].w, ch[i].n);
+                    R_.level_nodes[k]++;
+                    map.emplace(ch[i], p);
+                }
+                ls.gen = map_gen_[k];
+                ls.valid = true;
+                ls.term = ch[i].w[0];
+                ls.ptr = p;
+                out.w[out.n++] = p;
+                continue;
+            }
+            auto it = map.find(ch[i]);
             if (it != map.end()) {
                 p = it->second;
             } else {
@@ -395,6 +474,13 @@ class Builder {
     int nlev_;
     int s_[kMaxFormatLevels];
     std::vector<std::unordered_map<NodeKey, uint32_t, NodeKeyHash>> maps_;
+    static constexpr int kLeafCacheBits = 8;
+    struct LeafSlot {
+        uint32_t gen = 0, term = 0, ptr = 0;
+        bool valid = false;
+    };
+    std::vector<std::vector<LeafSlot>> leaf_cache_;
+    std::vector<uint32_t> map_gen_;
     int cb_[3];
     int cside_;
     std::vector<uint32_t> cache_;
@@ -503,7 +589,12 @@ class Decoder {
 
 }  // namespace
 
-VoxelSource* make_dense_source(const uint32_t* words, const int ldim[3]) { return new DenseSource(words, ldim); }
+VoxelSource* make_dense_source(const uint32_t* words, const int ldim[3]) {
+    return new DenseSource(words, nullptr, nullptr, ldim);
+}
+VoxelSource* make_palette_source(const uint8_t* idx, const uint32_t* palette, const int ldim[3]) {
+    return new DenseSource(nullptr, idx, palette, ldim);
+}
 VoxelSource* make_brick_source(const vx_grid* g) { return new BrickSource(g); }
 
 int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out) {

@@ -151,8 +151,10 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
     int rc = parse_spec(spec, &sp);
     if (rc) return rc;
     if (!grid) return fail(VX_EINVAL, "grid is NULL");
-    if ((grid->dense != nullptr) == (grid->fill_brick != nullptr))
-        return fail(VX_EINVAL, "set exactly one of grid->dense and grid->fill_brick");
+    if ((grid->dense != nullptr) + (grid->fill_brick != nullptr) + (grid->dense_pal != nullptr) != 1)
+        return fail(VX_EINVAL, "set exactly one of grid->dense, grid->dense_pal and grid->fill_brick");
+    if (grid->dense_pal && (!grid->palette || grid->palette[0] != 0))
+        return fail(VX_EINVAL, "grid->dense_pal needs a palette whose entry 0 is 0 (empty)");
     for (int i = 0; i < 3; i++)
         if ((int)grid->log2_dim[i] != sp.ldim[i])
             return fail(VX_EINVAL, "spec '%s' describes a 2^%d x 2^%d x 2^%d grid, the grid is 2^%u x 2^%u x 2^%u",
@@ -167,7 +169,9 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
     Volume& V = h->v;
     V.spec = sp;
     const double t0 = now_ms();
-    std::unique_ptr<VoxelSource> src(grid->dense ? make_dense_source(grid->dense, sp.ldim) : make_brick_source(grid));
+    std::unique_ptr<VoxelSource> src(grid->dense       ? make_dense_source(grid->dense, sp.ldim)
+                                     : grid->dense_pal ? make_palette_source(grid->dense_pal, grid->palette, sp.ldim)
+                                                       : make_brick_source(grid));
     rc = build_canonical(sp, *src, o.dedup_scope, &V.built);
     if (rc) return rc;
     const double t1 = now_ms();
@@ -434,6 +438,18 @@ extern "C" int vx_raygen_pinhole(const vx_camera* cam, vx_ray* rays, void* strea
     if (!rays) return fail(VX_EINVAL, "rays is NULL");
     if (!aligned(rays, 16)) return fail(VX_EINVAL, "rays must be 16-byte aligned");
     return launch_raygen(cp, rays, stream);
+}
+
+extern "C" int vx_raygen_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, uint32_t spp, float eps,
+                            float tmax, vx_ray* out, void* stream) {
+    clear_error();
+    if (n == 0 || spp == 0) return VX_OK;
+    if (spp > 1024) return fail(VX_EINVAL, "spp must be at most 1024");
+    if (!rays || !hits || !out) return fail(VX_EINVAL, "NULL array");
+    if (!aligned(rays, 16) || !aligned(hits, 16) || !aligned(out, 16))
+        return fail(VX_EINVAL, "rays, hits and out must be 16-byte aligned");
+    if (!(eps >= 0.0f) || !(tmax > 0.0f)) return fail(VX_EINVAL, "eps must be >= 0 and tmax > 0");
+    return launch_ao(rays, hits, n, seed, (int)spp, eps, tmax, out, stream);
 }
 
 extern "C" int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t hit_layout, const vx_trace_opts* opts,

@@ -45,9 +45,70 @@ __global__ void __launch_bounds__(256) k_raygen(CamDev cam, float4* __restrict__
     __stcs(rays + 2 * i, make_float4(r.o[0], r.o[1], r.o[2], r.tmin));
     __stcs(rays + 2 * i + 1, make_float4(r.d[0], r.d[1], r.d[2], r.tmax));
 }
+// Ambient-occlusion rays from primary hits: cosine-weighted about the
+// outward normal of the entered face (Malley's method: a uniform point on the
+// unit disk lifted to the hemisphere), two uniforms per ray from SplitMix64
+// (Steele, Lea & Flood 2014) of the counter (i * spp + k) * 2 + {0, 1} mixed
+// with the seed, top 24 bits.  The origin is the hit point moved eps along
+// the normal.  Misses and hits with no entry face give the empty ray (all
+// zero), which every trace reports as a miss.
+__host__ __device__ __forceinline__ uint64_t sm64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void __launch_bounds__(256) k_ao_rays(const float4* __restrict__ rays, const uint4* __restrict__ hits,
+                                                 uint64_t n, uint64_t seed_mix, int spp, float eps, float tmax,
+                                                 float4* __restrict__ out) {
+    const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n * (uint64_t)spp) return;
+    const uint64_t i = j / (uint64_t)spp;
+    const uint4 h = __ldg(hits + i);
+    const uint32_t status = h.w >> 24, face = (h.w >> 16) & 0xFFu;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (status == ST_HIT && face != 0) {
+        const int ax = (int)(face - 1) / 2;
+        const float sign = ((face - 1) & 1u) ? 1.0f : -1.0f;
+        const uint64_t c = j * 2u;
+        const float u1 = (float)(sm64(seed_mix ^ c) >> 40) * 0x1.0p-24f;
+        const float u2 = (float)(sm64(seed_mix ^ (c + 1)) >> 40) * 0x1.0p-24f;
+        const float r = sqrtf(u1);
+        float sp, cp;
+        sincospif(2.0f * u2, &sp, &cp);
+        const float lz = sqrtf(fmaxf(1.0f - u1, 0.0f));
+        float d[3] = {0.f, 0.f, 0.f};
+        const int a1 = ax == 2 ? 0 : ax + 1, a2 = ax == 0 ? 2 : ax - 1;
+#pragma unroll
+        for (int q = 0; q < 3; q++) d[q] = q == a1 ? r * cp : (q == a2 ? r * sp : (q == ax ? sign * lz : 0.f));
+        const float4 ra = __ldg(rays + 2 * i), rb = __ldg(rays + 2 * i + 1);
+        const float t = __uint_as_float(h.x);
+        float p[3] = {fmaf(t, rb.x, ra.x), fmaf(t, rb.y, ra.y), fmaf(t, rb.z, ra.z)};
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            if (q == ax) p[q] += sign * eps;
+        a = make_float4(p[0], p[1], p[2], 0.0f);
+        b = make_float4(d[0], d[1], d[2], tmax);
+    }
+    __stcs(out + 2 * j, a);
+    __stcs(out + 2 * j + 1, b);
+}
 }  // namespace
 
 void register_kernel_set(const KernelSet* ks) { registry().push_back(ks); }
+
+int launch_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, int spp, float eps, float tmax,
+              vx_ray* out, void* stream) {
+    const uint64_t m = n * (uint64_t)spp;
+    if (m == 0) return VX_OK;
+    k_ao_rays<<<(unsigned)((m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(rays), reinterpret_cast<const uint4*>(hits), n, sm64(seed), spp, eps, tmax,
+        reinterpret_cast<float4*>(out));
+    cudaError_t e = cudaGetLastError();
+    if (e) return fail(VX_ECUDA, "ao launch: %s", cudaGetErrorString(e));
+    return VX_OK;
+}
 
 const KernelSet* find_kernels(const std::string& spec) {
     for (const KernelSet* k : registry())

@@ -57,6 +57,7 @@ class VoxelSource {
 
 VoxelSource* make_dense_source(const uint32_t* words, const int ldim[3]);
 VoxelSource* make_brick_source(const vx_grid* g);
+VoxelSource* make_palette_source(const uint8_t* idx, const uint32_t* palette, const int ldim[3]);
 
 // ---------------------------------------------------------------------------
 // Canonical build (paper layout) and its statistics.
@@ -135,6 +136,8 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
+int launch_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, int spp, float eps, float tmax,
+              vx_ray* out, void* stream);
 struct BatchItemIn {
     const Volume* v;
     const vx_ray* rays;

@@ -57,6 +57,15 @@ def lib():
         L.sy_terrain.argtypes = [u64, i64, dbl, vp, vp]
         L.sy_incoherent_rays.argtypes = [u64, i64, i64, vp]
         L.sy_box_rays.argtypes = [u64, dbl, dbl, i64, vp]
+        L.sy_scene_new.restype = vp
+        L.sy_scene_new.argtypes = [u64, i64, ctypes.c_int, dbl, ctypes.c_int, ctypes.c_int]
+        L.sy_scene_free.argtypes = [vp]
+        L.sy_scene_palette.restype = vp
+        L.sy_scene_palette.argtypes = [vp]
+        L.sy_scene_instances.restype = i64
+        L.sy_scene_instances.argtypes = [vp]
+        L.sy_scene_render_u8.restype = i64
+        L.sy_scene_render_u8.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -179,3 +188,43 @@ def aimed_rays(seed: int, dims, count: int, dist: float = 3.0) -> np.ndarray:
     out[:, 3] = 0.0
     out[:, 7] = np.inf
     return out
+
+
+# --------------------------------------------------------------------------
+# Primitive scene (the 2048^3 workload)
+# --------------------------------------------------------------------------
+class PrimitiveScene:
+    """Seeded union of spheres (72%), boxes (24%) and thin walls (4%) in an
+    n^3 grid, plus 64 prototype 64^3 blocks stamped at 64-aligned bricks
+    (identical sub-volumes for DAG de-duplication); 16-colour palette.
+    Bricks are produced on demand by C callbacks (`fill_brick_fn`,
+    `block_empty_fn`, user pointer `handle`) that the builder calls directly;
+    `render_u8()` gives the whole grid as palette indices for the oracle."""
+
+    def __init__(self, seed: int, n: int = 2048, nprim: int = 20000, scale: float = 0.5,
+                 n_proto: int = 64, stamps_per_proto: int = 16):
+        assert n % 64 == 0
+        self.n = n
+        L = lib()
+        self.handle = ctypes.c_void_p(L.sy_scene_new(seed, n, nprim, scale, n_proto, stamps_per_proto))
+        pal = ctypes.cast(L.sy_scene_palette(self.handle), ctypes.POINTER(ctypes.c_uint32))
+        self.palette = np.ctypeslib.as_array(pal, shape=(256,)).copy()
+        self.instances = int(L.sy_scene_instances(self.handle))
+        self.fill_brick_fn = ctypes.cast(L.sy_scene_fill_brick, ctypes.c_void_p).value
+        self.block_empty_fn = ctypes.cast(L.sy_scene_block_empty, ctypes.c_void_p).value
+
+    def render_u8(self) -> np.ndarray:
+        g = np.empty((self.n, self.n, self.n), dtype=np.uint8)
+        self.occupied = int(lib().sy_scene_render_u8(self.handle, g.ctypes.data))
+        return g
+
+    def close(self):
+        if self.handle:
+            lib().sy_scene_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -272,3 +272,254 @@ void sy_box_rays(uint64_t seed, double N, double margin, int64_t n, float* out) 
         o[7] = INFINITY;
     }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Primitive scene (2048^3 workload): seeded spheres, axis-aligned boxes    */
+/* and thin walls in world space, plus 64 prototype 64^3 blocks (each a      */
+/* small composition of the same primitives) stamped at 64-aligned bricks,  */
+/* so identical 64^3 sub-volumes repeat.  Voxel value = palette index of the */
+/* last primitive covering the voxel centre (instances override their whole */
+/* brick); palette index 0 = empty.  Bricks of 64^3 are produced on demand.  */
+/* ---------------------------------------------------------------------- */
+enum { PR_SPHERE = 0, PR_BOX = 1 };
+typedef struct {
+    int type;
+    float a[3], b[3]; /* sphere: centre a, radius b[0]; box: [a, b) */
+    uint8_t color;
+} sy_prim;
+
+typedef struct {
+    int64_t n;          /* grid side */
+    int64_t nb;         /* bricks per axis (n / 64) */
+    int nprim;
+    sy_prim* prims;
+    int32_t* bin_start; /* nb^3 + 1 */
+    int32_t* bin_list;  /* primitive ids per brick, ascending */
+    uint8_t* protos;    /* 64 x 64^3 palette indices */
+    int32_t* inst;      /* per brick: prototype id or -1 */
+    uint32_t palette[256];
+    int64_t n_inst;
+} sy_scene;
+
+static double rnd(uint64_t seed, uint64_t i, uint64_t k) { return sy_u01(seed, i, k, 0x5C, 0); }
+
+static void prim_bbox(const sy_prim* p, double lo[3], double hi[3]) {
+    for (int i = 0; i < 3; i++) {
+        if (p->type == PR_SPHERE) { lo[i] = p->a[i] - p->b[0]; hi[i] = p->a[i] + p->b[0]; }
+        else { lo[i] = p->a[i]; hi[i] = p->b[i]; }
+    }
+}
+
+static void make_prim(uint64_t seed, uint64_t i, double extent, double scale, sy_prim* p) {
+    double u = rnd(seed, i, 0);
+    p->color = (uint8_t)(1 + (sy_hash(seed, i, 99, 0, 0) & 15));
+    double c[3];
+    for (int k = 0; k < 3; k++) c[k] = rnd(seed, i, 1 + k) * extent;
+    if (u < 0.72) { /* sphere, radius log-uniform in [2, 48] * scale */
+        p->type = PR_SPHERE;
+        double r = 2.0 * exp(rnd(seed, i, 4) * log(24.0)) * scale;
+        for (int k = 0; k < 3; k++) p->a[k] = (float)c[k];
+        p->b[0] = (float)r; p->b[1] = p->b[2] = 0.0f;
+    } else if (u < 0.96) { /* box, edges log-uniform in [2, 96] * scale */
+        p->type = PR_BOX;
+        for (int k = 0; k < 3; k++) {
+            double e = 2.0 * exp(rnd(seed, i, 5 + k) * log(48.0)) * scale;
+            p->a[k] = (float)floor(c[k] - e / 2); p->b[k] = (float)floor(c[k] + e / 2) + 1.0f;
+        }
+    } else { /* thin wall: 1-2 thick on one axis, 128-1024 long on the others */
+        p->type = PR_BOX;
+        int thin = (int)(sy_hash(seed, i, 98, 0, 0) % 3);
+        for (int k = 0; k < 3; k++) {
+            double e = k == thin ? 1.0 + (double)(sy_hash(seed, i, 97, k, 0) & 1)
+                                 : 128.0 * exp(rnd(seed, i, 8 + k) * log(8.0)) * (scale < 1 ? scale : 1);
+            p->a[k] = (float)floor(c[k] - e / 2); p->b[k] = p->a[k] + (float)floor(e);
+        }
+    }
+}
+
+static inline int prim_covers(const sy_prim* p, double x, double y, double z) {
+    if (p->type == PR_SPHERE) {
+        double dx = x - p->a[0], dy = y - p->a[1], dz = z - p->a[2];
+        return dx * dx + dy * dy + dz * dz <= (double)p->b[0] * p->b[0];
+    }
+    return x >= p->a[0] && x < p->b[0] && y >= p->a[1] && y < p->b[1] && z >= p->a[2] && z < p->b[2];
+}
+
+/* Rasterises primitives [ids] over the cube [x0, x0+s)^3 into out (s^3, x fastest). */
+static void raster(const sy_prim* prims, const int32_t* ids, int nids, int64_t x0, int64_t y0, int64_t z0, int64_t s,
+                   uint8_t* out) {
+    for (int q = 0; q < nids; q++) {
+        const sy_prim* p = &prims[ids[q]];
+        double lo[3], hi[3];
+        prim_bbox(p, lo, hi);
+        int64_t a[3], b[3];
+        const int64_t o[3] = {x0, y0, z0};
+        int skip = 0;
+        for (int k = 0; k < 3; k++) {
+            a[k] = (int64_t)floor(lo[k] - 0.5) - o[k];
+            b[k] = (int64_t)ceil(hi[k] + 0.5) - o[k];
+            if (a[k] < 0) a[k] = 0;
+            if (b[k] > s) b[k] = s;
+            if (a[k] >= b[k]) skip = 1;
+        }
+        if (skip) continue;
+        for (int64_t z = a[2]; z < b[2]; z++)
+            for (int64_t y = a[1]; y < b[1]; y++)
+                for (int64_t x = a[0]; x < b[0]; x++)
+                    if (prim_covers(p, x0 + x + 0.5, y0 + y + 0.5, z0 + z + 0.5)) out[x + s * (y + s * z)] = p->color;
+    }
+}
+
+sy_scene* sy_scene_new(uint64_t seed, int64_t n, int nprim, double scale, int n_proto, int stamps_per_proto) {
+    sy_scene* S = (sy_scene*)calloc(1, sizeof(sy_scene));
+    S->n = n;
+    S->nb = n / 64;
+    S->nprim = nprim;
+    S->prims = (sy_prim*)malloc(sizeof(sy_prim) * (nprim > 0 ? nprim : 1));
+    for (int i = 0; i < nprim; i++) make_prim(seed, (uint64_t)i, (double)n, scale, &S->prims[i]);
+    /* palette: 16 colours */
+    S->palette[0] = 0;
+    for (int c = 1; c < 256; c++) {
+        uint64_t h = sy_hash(seed ^ 0xC0102ull, (uint64_t)c, 0, 0, 0);
+        S->palette[c] = (uint32_t)(h & 0x00FFFFFFu) | 0xFF000000u;
+    }
+    /* bins: primitive ids per 64^3 brick */
+    const int64_t nb = S->nb, nbins = nb * nb * nb;
+    int32_t* cnt = (int32_t*)calloc((size_t)nbins, sizeof(int32_t));
+    for (int pass = 0; pass < 2; pass++) {
+        if (pass == 1) {
+            S->bin_start = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nbins + 1));
+            S->bin_start[0] = 0;
+            for (int64_t b = 0; b < nbins; b++) S->bin_start[b + 1] = S->bin_start[b] + cnt[b];
+            S->bin_list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(S->bin_start[nbins] + 1));
+            memset(cnt, 0, sizeof(int32_t) * (size_t)nbins);
+        }
+        for (int i = 0; i < nprim; i++) {
+            double lo[3], hi[3];
+            prim_bbox(&S->prims[i], lo, hi);
+            int64_t a[3], b[3];
+            for (int k = 0; k < 3; k++) {
+                a[k] = (int64_t)floor((lo[k] - 1.0) / 64.0);
+                b[k] = (int64_t)floor((hi[k] + 1.0) / 64.0);
+                if (a[k] < 0) a[k] = 0;
+                if (b[k] > nb - 1) b[k] = nb - 1;
+            }
+            for (int64_t z = a[2]; z <= b[2]; z++)
+                for (int64_t y = a[1]; y <= b[1]; y++)
+                    for (int64_t x = a[0]; x <= b[0]; x++) {
+                        int64_t bi = x + nb * (y + nb * z);
+                        if (pass == 1) S->bin_list[S->bin_start[bi] + cnt[bi]] = i;
+                        cnt[bi]++;
+                    }
+        }
+    }
+    free(cnt);
+    /* prototypes: each 6 primitives inside a 64^3 block */
+    S->protos = (uint8_t*)calloc((size_t)n_proto * 64 * 64 * 64 + 1, 1);
+    for (int pi = 0; pi < n_proto; pi++) {
+        sy_prim pp[6];
+        int32_t ids[6];
+        for (int q = 0; q < 6; q++) {
+            make_prim(seed ^ 0x9A0707ull, (uint64_t)(pi * 6 + q), 64.0, 0.5, &pp[q]);
+            ids[q] = q;
+        }
+        raster(pp, ids, 6, 0, 0, 0, 64, S->protos + (size_t)pi * 64 * 64 * 64);
+    }
+    /* instances: stamps_per_proto stamps of each prototype at seeded bricks */
+    S->inst = (int32_t*)malloc(sizeof(int32_t) * (size_t)nbins);
+    for (int64_t b = 0; b < nbins; b++) S->inst[b] = -1;
+    S->n_inst = 0;
+    for (int pi = 0; pi < n_proto; pi++)
+        for (int k = 0; k < stamps_per_proto; k++) {
+            uint64_t h = sy_hash(seed ^ 0x57A3Bull, (uint64_t)pi, (uint64_t)k, 0, 0);
+            int64_t bi = (int64_t)(h % (uint64_t)nbins);
+            if (S->inst[bi] < 0) S->n_inst++;
+            S->inst[bi] = pi;
+        }
+    return S;
+}
+
+void sy_scene_free(sy_scene* S) {
+    if (!S) return;
+    free(S->prims); free(S->bin_start); free(S->bin_list); free(S->protos); free(S->inst);
+    free(S);
+}
+
+const uint32_t* sy_scene_palette(const sy_scene* S) { return S->palette; }
+int64_t sy_scene_instances(const sy_scene* S) { return S->n_inst; }
+
+/* Palette indices of the 64^3 brick (bx, by, bz). */
+static void scene_brick_u8(const sy_scene* S, int64_t bx, int64_t by, int64_t bz, uint8_t* out) {
+    const int64_t bi = bx + S->nb * (by + S->nb * bz);
+    if (S->inst[bi] >= 0) {
+        memcpy(out, S->protos + (size_t)S->inst[bi] * 64 * 64 * 64, 64 * 64 * 64);
+        return;
+    }
+    memset(out, 0, 64 * 64 * 64);
+    raster(S->prims, S->bin_list + S->bin_start[bi], S->bin_start[bi + 1] - S->bin_start[bi], bx * 64, by * 64,
+           bz * 64, 64, out);
+}
+
+/* vx_fill_brick_fn-compatible callback: RGBA words of a cube (side 2^l2 <= 64,
+ * corner a multiple of the side), user = the scene. */
+int sy_scene_fill_brick(void* user, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t l2, uint32_t* out) {
+    const sy_scene* S = (const sy_scene*)user;
+    const int64_t s = (int64_t)1 << l2;
+    if (s > 64) {
+        for (int64_t z = 0; z < s; z += 64)
+            for (int64_t y = 0; y < s; y += 64)
+                for (int64_t x = 0; x < s; x += 64) {
+                    uint32_t* tmp = (uint32_t*)malloc(sizeof(uint32_t) * 64 * 64 * 64);
+                    sy_scene_fill_brick(user, x0 + (uint32_t)x, y0 + (uint32_t)y, z0 + (uint32_t)z, 6, tmp);
+                    for (int64_t zz = 0; zz < 64; zz++)
+                        for (int64_t yy = 0; yy < 64; yy++)
+                            memcpy(out + (x + s * ((y + yy) + s * (z + zz))), tmp + 64 * (yy + 64 * zz), 64 * 4);
+                    free(tmp);
+                }
+        return 0;
+    }
+    uint8_t* b = (uint8_t*)malloc(64 * 64 * 64);
+    const int64_t bx = x0 / 64, by = y0 / 64, bz = z0 / 64;
+    scene_brick_u8(S, bx, by, bz, b);
+    const int64_t ox = x0 % 64, oy = y0 % 64, oz = z0 % 64;
+    for (int64_t z = 0; z < s; z++)
+        for (int64_t y = 0; y < s; y++)
+            for (int64_t x = 0; x < s; x++)
+                out[x + s * (y + s * z)] = S->palette[b[(ox + x) + 64 * ((oy + y) + 64 * (oz + z))]];
+    free(b);
+    return 0;
+}
+
+/* vx_block_empty_fn-compatible: 1 only when no primitive or instance can
+ * touch the cube (side >= 64). */
+int sy_scene_block_empty(void* user, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t l2) {
+    const sy_scene* S = (const sy_scene*)user;
+    if (l2 < 6) return 0;
+    const int64_t k = (int64_t)1 << (l2 - 6);
+    for (int64_t bz = z0 / 64; bz < z0 / 64 + k; bz++)
+        for (int64_t by = y0 / 64; by < y0 / 64 + k; by++)
+            for (int64_t bx = x0 / 64; bx < x0 / 64 + k; bx++) {
+                const int64_t bi = bx + S->nb * (by + S->nb * bz);
+                if (S->inst[bi] >= 0 || S->bin_start[bi + 1] > S->bin_start[bi]) return 0;
+            }
+    return 1;
+}
+
+/* Whole grid as palette indices (n^3 bytes, x fastest). Returns occupied count. */
+int64_t sy_scene_render_u8(const sy_scene* S, uint8_t* grid) {
+    const int64_t nb = S->nb, n = S->n;
+    int64_t occ = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : occ)
+    for (int64_t bi = 0; bi < nb * nb * nb; bi++) {
+        uint8_t* b = (uint8_t*)malloc(64 * 64 * 64);
+        const int64_t bx = bi % nb, by = (bi / nb) % nb, bz = bi / (nb * nb);
+        scene_brick_u8(S, bx, by, bz, b);
+        for (int64_t z = 0; z < 64; z++)
+            for (int64_t y = 0; y < 64; y++) {
+                memcpy(grid + (bx * 64) + n * ((by * 64 + y) + n * (bz * 64 + z)), b + 64 * (y + 64 * z), 64);
+                for (int x = 0; x < 64; x++) occ += b[x + 64 * (y + 64 * z)] != 0;
+            }
+        free(b);
+    }
+    return occ;
+}

@@ -27,12 +27,13 @@ def gpu_keys(h, dims, layout=vx.HIT_FULL):
     return k, np.where(k >= 0, vx.STATUS_HIT, vx.STATUS_MISS)
 
 
-def compare(grid, rays, h, layout=vx.HIT_FULL, ref=None, ties=None):
-    """Returns a dict of counts; raises AssertionError when the rule fails."""
+def compare(grid, rays, h, layout=vx.HIT_FULL, ref=None, ties=None, palette=None):
+    """Returns a dict of counts; raises AssertionError when the rule fails.
+    grid: uint32 RGBA grid, or uint8 palette indices with `palette`."""
     nz, ny, nx = grid.shape
     dims = (nx, ny, nz)
     if ref is None:
-        ref, _ = oracle.trace(grid, rays)
+        ref, _ = oracle.trace(grid, rays) if palette is None else oracle.trace_pal(grid, palette, rays)
     rk = np.where(ref["status"] == oracle.HIT,
                   ref["x"].astype(np.int64) + nx * (ref["y"].astype(np.int64) + ny * ref["z"].astype(np.int64)), -1)
     gk, gst = gpu_keys(h, dims, layout)
@@ -47,7 +48,7 @@ def compare(grid, rays, h, layout=vx.HIT_FULL, ref=None, ties=None):
     n_tie_bad = 0
     if n_mis:
         if ties is None:
-            ties = oracle.classify(grid, rays)
+            ties = oracle.classify(grid, rays) if palette is None else oracle.classify_pal(grid, palette, rays)
         idx = np.nonzero(mism)[0]
         for i in idx:
             if ties["tie"][i]:

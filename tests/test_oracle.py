@@ -495,3 +495,54 @@ def test_terrain_small_is_deterministic():
     occ = (a != 0).mean()
     assert 0.1 < occ < 0.7
     assert len(np.unique(a)) <= 6
+
+
+# ---------------------------------------------------------------------------
+# Ambient-occlusion rays
+# ---------------------------------------------------------------------------
+def test_ao_rays_cosine_weighted_hemisphere():
+    g = synth.random_grid(51, (32, 32, 32), 0.1)
+    rays = synth.aimed_rays(52, (32, 32, 32), 4000)
+    h, _ = oracle.trace(g, rays)
+    spp = 16
+    ao = oracle.ao_rays(rays, h, seed=53, spp=spp, eps=1e-3, tmax=32.0)
+    hit = (h["status"] == oracle.HIT) & (h["face"] > 0)
+    assert hit.sum() > 1000
+    cos_all = []
+    for i in np.nonzero(hit)[0][:2000]:
+        a = (h["face"][i] - 1) // 2
+        sign = 1.0 if (h["face"][i] - 1) & 1 else -1.0
+        nrm = np.zeros(3); nrm[a] = sign
+        p = rays[i, 0:3].astype(np.float64) + h["t"][i] * rays[i, 4:7].astype(np.float64)
+        for k in range(spp):
+            r = ao[i * spp + k]
+            d = r[4:7].astype(np.float64)
+            assert abs(np.linalg.norm(d) - 1.0) < 1e-6
+            c = float(d @ nrm)
+            assert c >= 0.0
+            cos_all.append(c)
+            exp_o = p + 1e-3 * nrm
+            np.testing.assert_allclose(r[0:3], exp_o, rtol=0, atol=1e-4 * max(1.0, np.abs(exp_o).max()))
+            assert r[3] == 0.0 and r[7] == 32.0
+    cos_all = np.array(cos_all)
+    # cosine-weighted hemisphere: E[cos] = 2/3, E[cos^2] = 1/2 (uniform would give 1/2, 1/3)
+    assert abs(cos_all.mean() - 2 / 3) < 0.01
+    assert abs((cos_all ** 2).mean() - 0.5) < 0.01
+    # misses and face-0 hits give the all-zero ray, which traces as a miss
+    miss = np.nonzero(~hit)[0][:50]
+    for i in miss:
+        assert np.all(ao[i * spp:(i + 1) * spp] == 0)
+    hz, _ = oracle.trace(g, ao[[i * spp for i in miss]])
+    assert np.all(hz["status"] == oracle.MISS)
+
+
+def test_ao_rays_leave_the_hit_voxel():
+    g = synth.random_grid(54, (32, 32, 32), 0.15)
+    rays = synth.aimed_rays(55, (32, 32, 32), 3000)
+    h, _ = oracle.trace(g, rays)
+    ao = oracle.ao_rays(rays, h, seed=56, spp=4)
+    hit = np.nonzero((h["status"] == oracle.HIT) & (h["face"] > 0))[0]
+    hao, _ = oracle.trace(g, ao[np.repeat(hit, 4) * 4 + np.tile(np.arange(4), len(hit))])
+    hv = np.repeat(hit, 4)
+    same = (hao["status"] == oracle.HIT) & (hao["x"] == h["x"][hv]) & (hao["y"] == h["y"][hv]) & (hao["z"] == h["z"][hv])
+    assert not same.any()  # the origin sits outside the hit voxel, moving away from it
