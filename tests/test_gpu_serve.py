@@ -1,0 +1,102 @@
+"""Serving loop: continuous batching of render and trace requests over
+resident volumes.  Every request's hits must be identical alone and in the
+mix; memory admission defers requests that do not fit and refuses those
+larger than the whole budget."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2410_14128_b300 as vx
+from paper_2410_14128_b300 import serve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def volumes():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    t = synth.terrain_volume(301, 128)
+    n = synth.value_noise_volume(302, 64)
+    vols = {"terrain_rsg": vx.Volume("R(3,3,3) S(2) G(2)", t), "terrain_rrr": vx.Volume("R(3,3,3) R(2,2,2) R(2,2,2)", t),
+            "noise_s4r2": vx.Volume("S(4) R(2,2,2)", n)}
+    grids = {"terrain_rsg": t, "terrain_rrr": t, "noise_s4r2": n}
+    yield vols, grids
+    for v in vols.values():
+        v.free()
+
+
+def make_requests(seed, count, span_s, grids):
+    rng = np.random.default_rng(seed)
+    names = sorted(grids)
+    arrivals = np.cumsum(rng.exponential(span_s / count, count))
+    reqs = []
+    for i in range(count):
+        name = names[i % len(names)]
+        side = grids[name].shape[0]
+        if rng.random() < 0.5:
+            w, h = [(64, 64), (128, 96), (200, 150), (320, 180)][rng.integers(0, 4)]
+            cam = synth.camera(seed * 1000 + i, side, w, h, mode="above")
+            reqs.append(serve.Request(i, name, float(arrivals[i]), camera=cam))
+        else:
+            n = int(rng.integers(1, 60000))
+            rays = torch.from_numpy(synth.incoherent_rays(seed * 1000 + i, side, n)).pin_memory().numpy()
+            reqs.append(serve.Request(i, name, float(arrivals[i]), rays=rays))
+    return reqs
+
+
+def alone(vols, req):
+    v = vols[req.volume]
+    hits = vx.alloc_hits(req.n)
+    if req.camera is not None:
+        v.render(req.camera, hits)
+    else:
+        v.trace(torch.from_numpy(req.rays).cuda(), hits, mode=vx.MODE_PLAIN)
+    torch.cuda.synchronize()
+    return vx.hits_to_numpy(hits)
+
+
+def test_results_same_alone_and_in_the_mix(volumes):
+    vols, grids = volumes
+    reqs = make_requests(11, 60, 0.25, grids)
+    srv = serve.Server(vols, mem_budget_bytes=64 << 20)
+    res = srv.run(reqs, realtime=True)
+    assert len(res) == len(reqs)
+    assert srv.epochs > 1
+    for r in reqs:
+        out = res[r.id]
+        assert out.refused is None
+        assert np.array_equal(out.hits, alone(vols, r)), r.id
+        assert out.latency >= 0
+    # spot-check a few against the oracle
+    for r in reqs[:6]:
+        rays = oracle.pinhole(r.camera) if r.camera is not None else r.rays
+        from parity_util import compare
+        compare(grids[r.volume], rays, res[r.id].hits)
+    st = serve.latency_stats(res)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_memory_admission_defers_and_refuses(volumes):
+    vols, grids = volumes
+    reqs = make_requests(12, 20, 0.0, grids)
+    biggest = max(16 * r.n + (0 if r.camera is not None else 32 * r.n) for r in reqs)
+    huge = serve.Request(999, "terrain_rsg", 0.0,
+                         rays=np.zeros((biggest // 16, 8), np.float32))  # larger than the budget below
+    srv = serve.Server(vols, mem_budget_bytes=biggest + 1, max_inflight=4)
+    res = srv.run(reqs + [huge], realtime=False)
+    assert res[999].refused is not None and res[999].hits is None
+    for r in reqs:
+        assert res[r.id].refused is None
+        assert np.array_equal(res[r.id].hits, alone(vols, r))
+    assert srv.used == 0
+
+
+def test_serial_plain_path_same_results(volumes):
+    vols, grids = volumes
+    reqs = make_requests(13, 12, 0.05, grids)
+    res = serve.serve_serial(vols, reqs)
+    for r in reqs:
+        assert np.array_equal(res[r.id].hits, alone(vols, r))
