@@ -128,12 +128,22 @@ typedef struct vx_grid {
  *                 sub-volume (Sec. 4.3);
  *   device        CUDA device for the device image; -1 = current (default);
  *   no_upload     1 = build on the host only (vx_trace then fails);
- *   threads       host threads for the build, 0 = all cores. */
+ *   threads       host threads for the build, 0 = all cores;
+ *   canonical_device  1 = put the canonical words on the device as they
+ *                 are; 0 (default) = use the packed device layout when the
+ *                 volume is below 2^24 words: same offsets, but each pointer
+ *                 to an SVDAG node carries the node's valid mask in bits
+ *                 24..31 and an SVDAG slot of a leaf child holds the leaf's
+ *                 terminating integer, which saves one or two dependent reads
+ *                 per SVDAG level (vx_canonical always returns the paper's
+ *                 layout). */
 typedef struct vx_build_opts {
     int32_t dedup_scope;
     int32_t device;
     int32_t no_upload;
     int32_t threads;
+    int32_t canonical_device;
+    int32_t reserved[3];
 } vx_build_opts;
 
 /* Builds `spec` over `grid` and uploads it.  Paper: Sec. 4.1 (per-level
@@ -160,6 +170,8 @@ typedef struct vx_stats {
     uint32_t n_node_levels;  /* levels after expanding S(L)/G(L) into L octree levels */
     uint32_t log2_dim[3];
     int32_t specialized;     /* 1 = a compile-time-composed kernel serves this spec */
+    int32_t packed;          /* 1 = the device image uses the packed layout */
+    int32_t pad;
     uint64_t canonical_words;   /* paper-layout buffer size in words */
     uint64_t device_bytes;      /* device image size */
     uint64_t occupied_voxels;
@@ -240,14 +252,16 @@ int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, in
 /* Several ray sets, possibly through different volumes (all on one device),
  * in one call: the sets are grouped by format, each group (up to 64 sets) is
  * traced by one persistent kernel whose warps take rays from a queue that
- * spans all of the group's sets, and the groups' kernels run concurrently on
- * forked streams, sharing the SMs in proportion to their rays.  Hits of set k
+ * spans all of the group's sets, and the groups' kernels are enqueued on
+ * forked streams, each with a full GPU's worth of blocks, so that one
+ * group's blocks start as the previous group's retire.  Hits of set k
  * land in items[k].hits in the set's own order, exactly as vx_trace would
  * write them.  The call enqueues work on `stream` and returns; it allocates
  * nothing and does not synchronise, so it can be captured into a CUDA graph
  * (make one uncaptured call per device first: it creates the library's
- * fork streams).  opts: mode/refill/burst/block as for vx_trace (NULL or
- * VX_MODE_AUTO: the first volume's tuned options); sorting is not supported
+ * fork streams).  opts: refill/burst/block as for vx_trace (NULL or
+ * VX_MODE_AUTO: the first volume's tuned persistent options, else the
+ * defaults); sorting is not supported
  * here (VX_EUNSUPPORTED).  Calls for one device are enqueued one at a time.
  * (Not in the paper: it traces one frame of one format at a time.) */
 typedef struct vx_batch_item {

@@ -49,12 +49,13 @@ class _Grid(ctypes.Structure):
 
 class _BuildOpts(ctypes.Structure):
     _fields_ = [("dedup_scope", ctypes.c_int32), ("device", ctypes.c_int32), ("no_upload", ctypes.c_int32),
-                ("threads", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("canonical_device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_uint32), ("n_node_levels", ctypes.c_uint32), ("log2_dim", ctypes.c_uint32 * 3),
-                ("specialized", ctypes.c_int32), ("canonical_words", ctypes.c_uint64),
+                ("specialized", ctypes.c_int32), ("packed", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("canonical_words", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("occupied_voxels", ctypes.c_uint64),
                 ("level_words", ctypes.c_uint64 * MAX_LEVELS), ("level_nodes", ctypes.c_uint64 * MAX_LEVELS),
                 ("build_ms", ctypes.c_double), ("upload_ms", ctypes.c_double)]
@@ -184,7 +185,7 @@ class Volume:
 
     def __init__(self, spec: str, grid: np.ndarray | None = None, *, palette=None, log2_dim=None,
                  fill_brick=None, block_empty=None, user=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1,
-                 upload: bool = True):
+                 upload: bool = True, canonical_device: bool = False):
         """grid: dense (nz, ny, nx) uint32 RGBA array, or uint8 palette
         indices with `palette` (256 words); or log2_dim + fill_brick (a Python
         callable, or the address of a C function with the vx_fill_brick_fn
@@ -228,7 +229,7 @@ class Volume:
                 g.user = user.value if isinstance(user, ctypes.c_void_p) else user
         for i in range(3):
             g.log2_dim[i] = dims[i]
-        o = _BuildOpts(dedup, device, 0 if upload else 1, 0)
+        o = _BuildOpts(dedup, device, 0 if upload else 1, 0, 1 if canonical_device else 0)
         h = ctypes.c_void_p()
         _check(L.vx_build(spec.encode(), ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -265,7 +266,7 @@ class Volume:
         n = s.n_levels
         return {
             "n_levels": n, "n_node_levels": s.n_node_levels, "log2_dim": tuple(s.log2_dim),
-            "specialized": bool(s.specialized), "canonical_words": s.canonical_words,
+            "specialized": bool(s.specialized), "packed": bool(s.packed), "canonical_words": s.canonical_words,
             "canonical_bytes": 4 * s.canonical_words, "device_bytes": s.device_bytes,
             "occupied_voxels": s.occupied_voxels, "level_words": list(s.level_words)[:n],
             "level_nodes": list(s.level_nodes)[:n], "build_ms": s.build_ms, "upload_ms": s.upload_ms,

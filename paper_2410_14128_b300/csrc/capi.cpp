@@ -160,7 +160,7 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
             return fail(VX_EINVAL, "spec '%s' describes a 2^%d x 2^%d x 2^%d grid, the grid is 2^%u x 2^%u x 2^%u",
                         spec, sp.ldim[0], sp.ldim[1], sp.ldim[2], grid->log2_dim[0], grid->log2_dim[1],
                         grid->log2_dim[2]);
-    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0};
+    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, {0, 0, 0}};
     if (opts) o = *opts;
     if (o.dedup_scope != VX_DEDUP_WHOLE_LEVEL && o.dedup_scope != VX_DEDUP_PER_SUBVOLUME)
         return fail(VX_EINVAL, "bad dedup_scope %d", o.dedup_scope);
@@ -201,14 +201,19 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
         if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
         V.device = dev;
         const uint64_t bytes = V.built.words.size() * sizeof(uint32_t);
+        std::vector<uint32_t> packed;
+        const bool use_packed = !o.canonical_device && pack_device_image(sp, V.built.words, packed);
+        V.packed = use_packed ? 1 : 0;
+        const uint32_t* src_words = use_packed ? packed.data() : V.built.words.data();
         cudaError_t e = cudaMalloc((void**)&V.d_pool, bytes);
         if (e) return cuda_fail(e, "cudaMalloc (device image)");
-        e = cudaMemcpy(V.d_pool, V.built.words.data(), bytes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(V.d_pool, src_words, bytes, cudaMemcpyHostToDevice);
         if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
         V.pool_words = V.built.words.size();
         e = cudaMalloc((void**)&V.d_queue, kQueueRing * sizeof(unsigned long long));
         if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMalloc (queue counters)"); }
         st.device_bytes = bytes;
+        st.packed = V.packed;
         st.upload_ms = now_ms() - t1;
     }
     *out = h.release();

@@ -166,10 +166,10 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
-        e = v.kernels->trace_persistent(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), order, n, hits,
+        e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits,
                                         layout, block, bps, refill, burst, st, next);
     } else {
-        e = v.kernels->trace(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
+        e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
                              block, st);
     }
     if (scratch) cudaFreeAsync(scratch, st);
@@ -180,7 +180,7 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
 int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout,
                        const vx_trace_opts* o, void* stream, unsigned long long* counters) {
     const int block = pick_block(o);
-    int e = v.kernels->trace_count(v.spec.fmt, v.d_pool, reinterpret_cast<const float4*>(rays), n, hits, layout,
+    int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), n, hits, layout,
                                    block, (cudaStream_t)stream, counters);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
@@ -189,7 +189,7 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream) {
     const int block = pick_block(o);
-    int e = v.kernels->render(v.spec.fmt, v.d_pool, to_dev(cp), i0, n, hits, layout, block, (cudaStream_t)stream);
+    int e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block, (cudaStream_t)stream);
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }
@@ -224,13 +224,12 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         BatchDesc d;
     };
     std::vector<Sub> subs;
-    uint64_t total = 0;
     for (const BatchItemIn& it : items) {
         if (it.n == 0) continue;
-        total += it.n;
         Sub* g = nullptr;
         for (Sub& s2 : subs)
-            if (s2.ks == it.v->kernels && same_params(s2.v0->spec.fmt, it.v->spec.fmt) && s2.d.count < kBatchMax) {
+            if (s2.ks == it.v->kernels && same_params(s2.v0->spec.fmt, it.v->spec.fmt) &&
+                s2.d.packed == it.v->packed && s2.d.count < kBatchMax) {
                 g = &s2;
                 break;
             }
@@ -238,6 +237,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
             subs.push_back(Sub{it.v->kernels, it.v, BatchDesc{}});
             g = &subs.back();
             g->d.count = 0;
+            g->d.packed = it.v->packed;
             g->d.start[0] = 0;
         }
         const uint32_t k = g->d.count++;
@@ -247,11 +247,13 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         g->d.start[k + 1] = g->d.start[k] + it.n;
     }
     if (subs.empty()) return VX_OK;
+    // Options: explicit ones, else the first volume's tuned persistent-mode
+    // settings, else the defaults (plain-mode tunings do not carry over).
     vx_trace_opts def{};
     if (!o || o->mode == VX_MODE_AUTO) {
         Volume& mv = const_cast<Volume&>(*subs[0].v0);
         std::lock_guard<std::mutex> lock(mv.tune_mu);
-        def = mv.tuned ? mv.tuned_opts : vx_trace_opts{};
+        if (mv.tuned && mv.tuned_opts.mode == VX_MODE_PERSISTENT) def = mv.tuned_opts;
     } else {
         def = *o;
     }
@@ -280,8 +282,12 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         int per_sm = 1;
         int rc = g.ks->resident_blocks(layout, block, &per_sm);
         if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
+        // Every launch gets a full GPU's worth of resident blocks: the
+        // launches run one after another in effect, each draining its queue
+        // with all SMs, and the next one's blocks start as the previous one's
+        // retire (separate streams), so no SM waits for a slower group.
         const uint64_t n = g.d.start[g.d.count];
-        uint64_t grid = (uint64_t)((double)sms * per_sm * (double)n / (double)total + 0.999);
+        uint64_t grid = (uint64_t)sms * per_sm;
         const uint64_t need = (n + block - 1) / block;
         if (grid > need) grid = need;
         if (grid < 1) grid = 1;

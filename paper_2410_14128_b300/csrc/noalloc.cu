@@ -54,7 +54,7 @@ int scratch_address(int dev, unsigned int** out) {
 // (same refill scheme as k_trace_persistent: a warp with >= `refill` idle
 // lanes takes that many ray indices with one atomic).
 template <int LAYOUT>
-__global__ void __launch_bounds__(256) k_trace_noalloc(DynF f, const uint32_t* __restrict__ pool,
+__global__ void __launch_bounds__(256) k_trace_noalloc(DynF f, const Img pool,
                                                        const float4* __restrict__ rays, uint32_t n,
                                                        void* __restrict__ hits, unsigned int* next, int refill,
                                                        int burst) {
@@ -136,10 +136,10 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     DynF f;
     f.p = V.spec.fmt;
     if (layout == VX_HIT_FULL)
-        k_trace_noalloc<0><<<(unsigned)grid, block, 0, st>>>(f, V.d_pool, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<0><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     else
-        k_trace_noalloc<1><<<(unsigned)grid, block, 0, st>>>(f, V.d_pool, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<1><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "vx_trace_noalloc launch: %s", cudaGetErrorString(e));

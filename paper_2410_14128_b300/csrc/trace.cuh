@@ -232,6 +232,15 @@ __device__ __forceinline__ bool near32(float x, float y) {
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint32_t i) { return __ldg(pool + i); }
 
+// A volume's device image: its words, and whether they are in the packed
+// layout (pack.cpp: pointers to SVDAG nodes carry the node's valid mask in
+// bits 24..31; SVDAG slots of leaf children hold the terminating integer).
+struct Img {
+    const uint32_t* w;
+    int packed;
+};
+constexpr uint32_t kPtrMask = 0x00FFFFFFu;
+
 // ---------------------------------------------------------------------------
 // The traversal
 // ---------------------------------------------------------------------------
@@ -251,17 +260,31 @@ struct Walker {
     RayIn r;
     float inv[3];
     float tx, tcur;
+    float gabs;  // guard band: 2^-20 of the largest |t| this walk compares
     int sg[3];
     int v0[3], c[3];
-    int j, la, lp, it;
+    int j, la, lp, budget;
+    int kind_c, s_c, b_c[3];  // node level j: kind, children side, fanout (cached)
+    bool bot_c;
     bool fresh;
     uint32_t Pc, Mc;  // node of level j (also kept in P[j], M[j])
     uint32_t* P;      // per-level node stack, F::kMaxJ entries each, owned by
     uint32_t* M;      // the caller (kept outside so the scalars stay in registers)
     Cnt cnt;
 
-    __device__ __forceinline__ bool start(const F& f, const uint32_t* __restrict__ pool, const RayIn& ray,
-                                          HitRec& out) {
+    __device__ __forceinline__ void load_level(const F& f) {
+        kind_c = f.kind(j);
+        s_c = f.s(j);
+        bot_c = f.bot(j);
+        if (j == 0) { b_c[0] = f.b0(0); b_c[1] = f.b0(1); b_c[2] = f.b0(2); }
+        else { b_c[0] = b_c[1] = b_c[2] = f.b(j); }
+    }
+
+    // |x - y| within the guard band (true for NaN: decide in FP64)
+    __device__ __forceinline__ bool near(float x, float y) const { return !(fabsf(x - y) > gabs); }
+
+    __device__ __forceinline__ bool start(const F& f, const Img im, const RayIn& ray, HitRec& out) {
+        const uint32_t* __restrict__ pool = im.w;
         r = ray;
         // Invalid rays: any NaN, or an infinite tmin.
         if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
@@ -360,6 +383,7 @@ struct Walker {
             const int k0 = f.kind(0);
             if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
             else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+            else if (im.packed) { P[0] = root & kPtrMask; M[0] = root >> 24; }
             else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
         }
         j = 0;
@@ -374,25 +398,28 @@ struct Walker {
         lp = ea >= 0 ? (sel3(sg, ea) > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
         tcur = te;
         fresh = true;  // no step taken yet
-        it = 0;
+        // Every crossing this walk compares lies in [min(te, tx), max(te, tx)]
+        // (crossings past the exit end it), and the FP32 error of one is at
+        // most 3 2^-24 |t|: a band of 2^-20 max|t| covers both operands 16x.
+        gabs = kGuard * fmaxf(fabsf(te), fabsf(tx));
+        // A ray crosses at most nx + ny + nz cells of any level and each step
+        // costs at most J descents; past this bound the ray reports ST_ERROR.
+        budget = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (f.J() + 2);
+        load_level(f);
         return false;
     }
 
-    __device__ __forceinline__ bool step(const F& f, const uint32_t* __restrict__ pool, HitRec& out) {
-        // A ray crosses at most nx + ny + nz cells of any level and each step
-        // costs at most J descents; past this bound the ray reports ST_ERROR.
-        const int J = f.J();
-        const int cap = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (J + 2);
-        if (++it > cap) {
+    __device__ __forceinline__ bool step(const F& f, const Img im, HitRec& out) {
+        const uint32_t* __restrict__ pool = im.w;
+        if (--budget < 0) {
             out = miss_rec(ST_ERROR);
             return true;
         }
         VX_CNT(iters, 1);
-        const int kind = f.kind(j);
-        const int s = f.s(j);
-        int bx, by, bz;
-        if (j == 0) { bx = f.b0(0); by = f.b0(1); bz = f.b0(2); }
-        else { bx = by = bz = f.b(j); }
+        const int J = f.J();
+        const int kind = kind_c;
+        const int s = s_c;
+        const int bx = b_c[0], by = b_c[1], bz = b_c[2];
         const uint32_t lx = (uint32_t)c[0] & ((1u << bx) - 1u);
         const uint32_t ly = (uint32_t)c[1] & ((1u << by) - 1u);
         const uint32_t lz = (uint32_t)c[2] & ((1u << bz) - 1u);
@@ -415,13 +442,19 @@ struct Walker {
                 const uint32_t rank = __popc(Mc & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = Pc + 2u * rank;
-                    if (f.bot(j)) { term = ldw(pool, addr); VX_CNT(bytes, 4); }
+                    if (bot_c) { term = ldw(pool, addr); VX_CNT(bytes, 4); }
                     else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
                     const uint32_t cp = ldw(pool, Pc + 1u + rank);
-                    if (f.bot(j)) term = ldw(pool, cp);
-                    else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
-                    VX_CNT(bytes, 8);
+                    if (im.packed) {
+                        if (bot_c) term = cp;
+                        else { Pn = cp & kPtrMask; Mn = cp >> 24; node_ready = true; }
+                        VX_CNT(bytes, 4);
+                    } else {
+                        if (bot_c) term = ldw(pool, cp);
+                        else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
+                        VX_CNT(bytes, 8);
+                    }
                 }
             }
             if (j == J - 1) {
@@ -436,6 +469,7 @@ struct Walker {
                 const int nk = f.kind(j + 1);
                 if (nk == K_RAW) { Pn = term; }
                 else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
+                else if (im.packed) { Pn = term & kPtrMask; Mn = term >> 24; }
                 else { Pn = term; Mn = ldw(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
@@ -443,7 +477,8 @@ struct Walker {
             M[j] = Mn;
             Pc = Pn;
             Mc = Mn;
-            const int sn = f.s(j), bn = f.b(j);
+            load_level(f);
+            const int sn = s_c, bn = b_c[0];
             const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
 #pragma unroll
             for (int i = 0; i < 3; i++) {
@@ -488,7 +523,7 @@ struct Walker {
         bool und = false;
 #pragma unroll
         for (int i = 0; i < 3; i++)
-            if (sg[i] != 0 && i != a && near32(tm, tn[i])) und = true;
+            if (sg[i] != 0 && i != a && near(tm, tn[i])) und = true;
         if (und) {
             VX_CNT(fp64, 1);
             a = argmin64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], pl[0], pl[1], pl[2]);
@@ -499,7 +534,7 @@ struct Walker {
         const int pla = sel3(pl, a), sga = sel3(sg, a);
         bool out_now = pla == (sga > 0 ? (1 << f.ldim(a)) : 0);
         if (!out_now) {
-            if (near32(tm, tx)) {
+            if (near(tm, tx)) {
                 VX_CNT(fp64, 1);
                 out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
                                   f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
@@ -534,6 +569,7 @@ struct Walker {
             j = jp;
             Pc = P[j];
             Mc = M[j];
+            load_level(f);
         }
         return false;
     }
@@ -541,7 +577,7 @@ struct Walker {
 #undef VX_CNT
 
 template <bool COUNT, class F>
-__device__ __forceinline__ HitRec trace_ray(const F& f, const uint32_t* __restrict__ pool, const RayIn& r, Cnt& cnt) {
+__device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt) {
     uint32_t P[F::kMaxJ], M[F::kMaxJ];
     Walker<COUNT, F> w;
     w.P = P;
@@ -619,7 +655,7 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // `order` (optional): launch slot k traces ray order[k] and writes its hit
 // at order[k] (rays sorted for coherence, results in the caller's order).
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256) k_trace(F f, const uint32_t* __restrict__ pool, const float4* __restrict__ rays,
+__global__ void __launch_bounds__(256) k_trace(F f, const Img pool, const float4* __restrict__ rays,
                                                const uint32_t* __restrict__ order, uint64_t n,
                                                void* __restrict__ hits) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -635,7 +671,7 @@ __global__ void __launch_bounds__(256) k_trace(F f, const uint32_t* __restrict__
 // counters in counters[0..2] (bytes of the format read, iterations, FP64
 // decisions), summed per warp then added atomically.
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __restrict__ pool,
+__global__ void __launch_bounds__(256) k_trace_count(F f, const Img pool,
                                                      const float4* __restrict__ rays, uint64_t n,
                                                      void* __restrict__ hits, unsigned long long* counters) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -666,7 +702,7 @@ __global__ void __launch_bounds__(256) k_trace_count(F f, const uint32_t* __rest
 // walking.  Each round advances every live lane by up to `burst` iterations.
 // `next` must be zero at launch; the kernel leaves it >= n.
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t* __restrict__ pool,
+__global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
                                                           const uint32_t* __restrict__ order, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
@@ -721,6 +757,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_persistent(F f, const uint32_t
 constexpr int kBatchMax = 64;
 struct BatchDesc {
     uint32_t count;
+    int packed;  // layout of every volume of the launch
     const uint32_t* pool[kBatchMax];
     const float4* rays[kBatchMax];
     void* hits[kBatchMax];
@@ -741,7 +778,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_batch(F f, const __grid_consta
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
     int set = 0;
-    const uint32_t* pool = nullptr;
+    Img pool{nullptr, desc.packed};
     void* hits = nullptr;
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
@@ -765,7 +802,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_batch(F f, const __grid_consta
                     }
                     set = lo;
                     idx = slot - desc.start[set];
-                    pool = desc.pool[set];
+                    pool.w = desc.pool[set];
                     hits = desc.hits[set];
                     HitRec h;
                     if (w.start(f, pool, load_ray(desc.rays[set], idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
@@ -788,7 +825,7 @@ __global__ void __launch_bounds__(256, 3) k_trace_batch(F f, const __grid_consta
 }
 
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256) k_render(F f, const uint32_t* __restrict__ pool, CamDev cam, uint64_t i0,
+__global__ void __launch_bounds__(256) k_render(F f, const Img pool, CamDev cam, uint64_t i0,
                                                 uint64_t n, void* __restrict__ hits) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -806,13 +843,13 @@ struct KernelSet {
     const char* spec;
     bool specialized;
     FmtParams params;
-    int (*trace)(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order, uint64_t n,
+    int (*trace)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
                  void* hits, int layout, int block, cudaStream_t st);
-    int (*render)(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
+    int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
-    int (*trace_count)(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+    int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                        int layout, int block, cudaStream_t st, unsigned long long* counters);
-    int (*trace_persistent)(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order,
+    int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
                             cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
@@ -824,7 +861,7 @@ struct KernelSet {
 template <class F>
 struct Launch {
     static F make(const FmtParams& p);
-    static int trace(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order, uint64_t n,
+    static int trace(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
                      void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);
@@ -833,7 +870,7 @@ struct Launch {
         else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
         return (int)cudaGetLastError();
     }
-    static int trace_count(const FmtParams& p, const uint32_t* pool, const float4* rays, uint64_t n, void* hits,
+    static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                            int layout, int block, cudaStream_t st, unsigned long long* counters) {
         if (n == 0) return 0;
         const F f = make(p);
@@ -843,7 +880,7 @@ struct Launch {
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
-    static int trace_persistent(const FmtParams& p, const uint32_t* pool, const float4* rays, const uint32_t* order,
+    static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
                                 int burst, cudaStream_t st, unsigned long long* next) {
         if (n == 0) return 0;
@@ -888,7 +925,7 @@ struct Launch {
         else k_trace_batch<F, 1><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
         return (int)cudaGetLastError();
     }
-    static int render(const FmtParams& p, const uint32_t* pool, const CamDev& cam, uint64_t i0, uint64_t n,
+    static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
                       void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);

@@ -71,6 +71,10 @@ struct BuildResult {
 
 int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out);
 
+// Device image in the packed layout (same offsets); false when the volume is
+// too large for it or has no SVDAG level (then the canonical words are used).
+bool pack_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out);
+
 // Decodes the cube (side 2^log2s at x0,y0,z0) from a canonical buffer.
 int decode_cube(const Spec& spec, const uint32_t* words, uint64_t nwords, int64_t x0, int64_t y0, int64_t z0,
                 int log2s, uint32_t* out);
@@ -107,6 +111,7 @@ struct Volume {
     int device = -1;
     uint32_t* d_pool = nullptr;
     uint64_t pool_words = 0;
+    int packed = 0;  // device image in the packed layout (pack.cpp)
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
     Staging staging;

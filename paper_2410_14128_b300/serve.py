@@ -48,6 +48,12 @@ class Request:
         return int(self.rays.shape[0])
 
 
+def digest(hits: np.ndarray) -> tuple:
+    """Cheap fingerprint of a hit array (xor and sum of its 64-bit words)."""
+    a = np.ascontiguousarray(hits).view(np.uint64)
+    return (int(np.bitwise_xor.reduce(a)), int(a.sum(dtype=np.uint64)), a.size)
+
+
 @dataclasses.dataclass
 class Result:
     id: int
@@ -56,6 +62,7 @@ class Result:
     admitted: float
     done: float
     refused: str | None = None
+    digest: tuple | None = None
 
     @property
     def latency(self) -> float:
@@ -64,7 +71,7 @@ class Result:
 
 class Server:
     def __init__(self, volumes: dict, mem_budget_bytes: int, max_inflight: int = 256, streams: int = 3,
-                 layout: int = HIT_FULL, clock=time.perf_counter):
+                 layout: int = HIT_FULL, clock=time.perf_counter, keep_hits: bool = True, digest_every: int = 1):
         import torch
         self.torch = torch
         self.volumes = volumes
@@ -80,6 +87,8 @@ class Server:
         self.inflight: list = []  # (req, admitted_time, bytes, event, host_hits, keep)
         self.results: dict = {}
         self.epochs = 0
+        self.keep_hits = keep_hits  # else keep only a digest of each result
+        self.digest_every = max(1, digest_every)  # digest request ids divisible by this
 
     def now(self) -> float:
         return self.clock() - self.t0
@@ -149,7 +158,8 @@ class Server:
             if ev.query():
                 t = self.now()
                 h = host.numpy().view(hit_dtype(self.layout)).reshape(-1)
-                self.results[req.id] = Result(req.id, h, req.arrival, adm, t)
+                dg = digest(h) if req.id % self.digest_every == 0 else None
+                self.results[req.id] = Result(req.id, h if self.keep_hits else None, req.arrival, adm, t, digest=dg)
                 self.used -= need
                 done += 1
             else:
@@ -184,7 +194,8 @@ class Server:
         return self.results
 
 
-def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.perf_counter) -> dict:
+def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.perf_counter,
+                 keep_hits: bool = True, digest_every: int = 1) -> dict:
     """The plain path: one request at a time, in arrival order, each traced by
     its own launch (render, or copy + plain trace) and waited for."""
     import torch
@@ -204,7 +215,10 @@ def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.per
             rays = torch.from_numpy(req.rays).cuda()
             vol.trace(rays, hits, layout, mode=MODE_PLAIN)
         h = hits.cpu().numpy().view(hit_dtype(layout)).reshape(-1)
-        results[req.id] = Result(req.id, h, req.arrival, start, clock() - t0)
+        done = clock() - t0
+        dg = digest(h) if req.id % max(1, digest_every) == 0 else None
+        results[req.id] = Result(req.id, h if keep_hits else None, req.arrival, start, done, digest=dg)
+        del hits
     return results
 
 

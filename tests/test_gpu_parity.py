@@ -371,3 +371,16 @@ def test_batch_in_cuda_graph():
         for (v, r_np), (_, r, h) in zip(sets, dev):
             if len(r_np):
                 assert np.array_equal(vx.hits_to_numpy(h), gpu_trace(vols[v], r_np, mode=vx.MODE_PLAIN)), rep
+
+
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "G(7)", "R(2,2,2) G(2) G(3)", "S(2) G(2) R(3,3,3)"])
+def test_packed_device_image_equals_canonical(spec):
+    g = synth.terrain_volume(87, 128)
+    rays = np.concatenate([synth.incoherent_rays(88, 128, 40000),
+                           oracle.pinhole(synth.camera(89, 128, 160, 120, mode="above"))])
+    packed = vx.Volume(spec, g)
+    canon = vx.Volume(spec, g, canonical_device=True)
+    assert packed.stats()["packed"] and not canon.stats()["packed"]
+    a = gpu_trace(packed, rays)
+    assert np.array_equal(a, gpu_trace(canon, rays))
+    compare(g, rays, a)
