@@ -185,7 +185,7 @@ class Volume:
 
     def __init__(self, spec: str, grid: np.ndarray | None = None, *, palette=None, log2_dim=None,
                  fill_brick=None, block_empty=None, user=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1,
-                 upload: bool = True, canonical_device: bool = False):
+                 upload: bool = True, canonical_device: bool = False, threads: int = 0):
         """grid: dense (nz, ny, nx) uint32 RGBA array, or uint8 palette
         indices with `palette` (256 words); or log2_dim + fill_brick (a Python
         callable, or the address of a C function with the vx_fill_brick_fn
@@ -229,7 +229,7 @@ class Volume:
                 g.user = user.value if isinstance(user, ctypes.c_void_p) else user
         for i in range(3):
             g.log2_dim[i] = dims[i]
-        o = _BuildOpts(dedup, device, 0 if upload else 1, 0, 1 if canonical_device else 0)
+        o = _BuildOpts(dedup, device, 0 if upload else 1, threads, 1 if canonical_device else 0)
         h = ctypes.c_void_p()
         _check(L.vx_build(spec.encode(), ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -27,6 +27,7 @@
 //     level with VX_DEDUP_WHOLE_LEVEL (Sec. 4.3).
 // A terminating integer is the word offset of the next level's sub-volume,
 // or the voxel's RGBA at the last level; 0 is empty (Sec. 3.3).
+#include <omp.h>
 #include <string.h>
 
 #include <algorithm>
@@ -87,6 +88,7 @@ class DenseSource final : public VoxelSource {
                     }
         }
     }
+    bool thread_safe() const override { return true; }
     bool empty(int64_t x0, int64_t y0, int64_t z0, int s) override {
         if (s >= levels_) s = levels_ - 1;
         return !bit(s, x0 >> s, y0 >> s, z0 >> s);
@@ -280,6 +282,20 @@ struct NodeKeyHash {
     }
 };
 
+// What a write holds, for relocating it when fragments are merged.
+enum WriteTag : uint8_t {
+    T_RAW = 0,        // Raw array (pointers to level k+1 unless k is last)
+    T_SVO_ROOT,       // SVO root node {children list, masks}
+    T_DAG_ROOT,       // SVDAG root node (not de-duplicated)
+    T_SVO_LIST,       // contiguous internal SVO nodes
+    T_SVO_LIST_LEAF,  // contiguous leaf SVO nodes {terminating integer, 0}
+    T_DAG_CHILD,      // de-duplicated SVDAG node (1 word = leaf)
+};
+struct WriteRec {
+    uint32_t off, n;
+    uint8_t tag, level;
+};
+
 class Builder {
   public:
     Builder(const Spec& sp, VoxelSource& src, int scope, BuildResult& R) : sp_(sp), src_(src), scope_(scope), R_(R) {
@@ -302,14 +318,76 @@ class Builder {
         std::vector<uint32_t> data;
         const int64_t lo[3] = {0, 0, 0};
         if (construct(0, lo, data)) {
-            uint32_t p = write(0, data.data(), data.size());
+            uint32_t p = write(0, data.data(), data.size(), root_tag(0));
             if (!err_) R_.words[0] = p;
         }
         return err_;
     }
 
+    // Parallel build for a Raw top level over a thread-safe source: every
+    // top cell's sub-volume is built as a fragment (own buffer, own maps,
+    // write log) on its own thread; the fragments are then appended in the
+    // Morton order of their cells, pointers relocated and SVDAG nodes looked
+    // up in this builder's maps, so the buffer equals the sequential one.
+    int run_parallel(int threads) {
+        const Level& L0 = sp_.lv[0];
+        const uint64_t cells = 1ull << (L0.e[0] + L0.e[1] + L0.e[2]);
+        struct Frag {
+            std::vector<uint32_t> words;
+            std::vector<WriteRec> log;
+            uint32_t root = 0;
+            uint64_t occupied = 0;
+            int err = 0;
+            std::string msg;
+        };
+        std::vector<Frag> frags(cells);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads)
+        for (int64_t m = 0; m < (int64_t)cells; m++) {
+            uint32_t c[3];
+            morton_decode((uint64_t)m, L0.e, c);
+            const int64_t lo[3] = {(int64_t)c[0] << s_[0], (int64_t)c[1] << s_[0], (int64_t)c[2] << s_[0]};
+            Frag& F = frags[(size_t)m];
+            if (src_.empty(lo[0], lo[1], lo[2], s_[0])) continue;
+            BuildResult local;
+            local.words.assign(1, 0u);  // offsets start at 1: 0 stays "empty"
+            Builder b(sp_, src_, scope_, local);
+            b.log_ = &F.log;
+            std::vector<uint32_t> data;
+            if (b.construct(1, lo, data)) F.root = b.write(1, data.data(), data.size(), b.root_tag(1));
+            F.err = b.err_;
+            if (F.err) F.msg = vx_last_error();
+            F.words.swap(local.words);
+            F.occupied = local.occupied;
+        }
+        R_.words.assign(1, 0u);
+        std::vector<uint32_t> top((size_t)cells, 0u);
+        bool any = false;
+        for (uint64_t m = 0; m < cells && !err_; m++) {
+            Frag& F = frags[(size_t)m];
+            if (F.err) return fail(F.err, "%s", F.msg.c_str());
+            R_.occupied += F.occupied;
+            if (!F.root) continue;
+            uint32_t c[3];
+            morton_decode(m, L0.e, c);
+            top[(size_t)(c[0] + ((uint64_t)c[1] << L0.e[0]) + ((uint64_t)c[2] << (L0.e[0] + L0.e[1])))] = merge(F.words, F.log, F.root);
+            any = true;
+            std::vector<uint32_t>().swap(F.words);
+            std::vector<WriteRec>().swap(F.log);
+        }
+        if (any && !err_) {
+            R_.words[0] = write(0, top.data(), top.size(), T_RAW);
+            R_.level_nodes[0]++;
+        }
+        return err_;
+    }
+
   private:
-    uint32_t write(int k, const uint32_t* w, size_t n) {
+    uint8_t root_tag(int k) const {
+        const int kind = sp_.lv[k].kind;
+        return kind == K_RAW ? T_RAW : (kind == K_SVO ? T_SVO_ROOT : T_DAG_ROOT);
+    }
+
+    uint32_t write(int k, const uint32_t* w, size_t n, uint8_t tag) {
         if (R_.words.size() + n > 0xFFFFFFFFull) {
             err_ = fail(VX_ETOOBIG, "format buffer exceeds 2^32 words (16 GiB, Sec. 3.3)");
             return 0;
@@ -317,7 +395,61 @@ class Builder {
         uint32_t off = (uint32_t)R_.words.size();
         R_.words.insert(R_.words.end(), w, w + n);
         R_.level_words[k] += n;
+        if (log_) log_->push_back(WriteRec{off, (uint32_t)n, tag, (uint8_t)k});
         return off;
+    }
+
+    // Appends one fragment; returns the global offset of its root.
+    uint32_t merge(const std::vector<uint32_t>& fw, const std::vector<WriteRec>& log, uint32_t root) {
+        std::vector<uint32_t> reloc(fw.size(), 0u);
+        std::vector<uint32_t> tmp;
+        for (const WriteRec& r : log) {
+            if (err_) return 0;
+            const int k = r.level;
+            const bool last = k == nlev_ - 1;
+            tmp.assign(fw.begin() + r.off, fw.begin() + r.off + r.n);
+            switch (r.tag) {
+                case T_RAW:
+                    if (!last)
+                        for (uint32_t& x : tmp)
+                            if (x) x = reloc[x];
+                    break;
+                case T_SVO_ROOT:
+                case T_SVO_LIST:
+                    for (size_t i = 0; i < tmp.size(); i += 2) tmp[i] = reloc[tmp[i]];
+                    break;
+                case T_SVO_LIST_LEAF:
+                    if (!last)
+                        for (size_t i = 0; i < tmp.size(); i += 2) tmp[i] = reloc[tmp[i]];
+                    break;
+                default:  // SVDAG node: a leaf word, or masks + child pointers
+                    if (tmp.size() == 1) {
+                        if (!last) tmp[0] = reloc[tmp[0]];
+                    } else {
+                        for (size_t i = 1; i < tmp.size(); i++) tmp[i] = reloc[tmp[i]];
+                    }
+            }
+            uint32_t g;
+            if (r.tag == T_DAG_CHILD && scope_ == VX_DEDUP_WHOLE_LEVEL) {
+                NodeKey key;
+                key.n = (uint32_t)tmp.size();
+                for (uint32_t i = 0; i < key.n; i++) key.w[i] = tmp[i];
+                auto it = maps_[k].find(key);
+                if (it != maps_[k].end()) {
+                    g = it->second;
+                } else {
+                    g = write(k, tmp.data(), tmp.size(), r.tag);
+                    R_.level_nodes[k]++;
+                    maps_[k].emplace(key, g);
+                }
+            } else {
+                g = write(k, tmp.data(), tmp.size(), r.tag);
+                if (r.tag == T_SVO_LIST || r.tag == T_SVO_LIST_LEAF) R_.level_nodes[k] += r.n / 2;
+                else R_.level_nodes[k]++;
+            }
+            reloc[r.off] = g;
+        }
+        return reloc[root];
     }
 
     uint32_t voxel(const int64_t v[3]) {
@@ -341,7 +473,7 @@ class Builder {
         if (src_.empty(lo[0], lo[1], lo[2], s_[k])) return 0;
         std::vector<uint32_t> data;
         if (!construct(k + 1, lo, data)) return 0;
-        return write(k + 1, data.data(), data.size());
+        return write(k + 1, data.data(), data.size(), root_tag(k + 1));
     }
 
     // Sub-volume of level k at lo; false if it is empty.
@@ -399,7 +531,7 @@ class Builder {
         uint32_t n = 0;
         for (int i = 0; i < 8; i++)
             if ((valid >> i) & 1u) { buf[n++] = ch[i].w[0]; buf[n++] = ch[i].w[1]; }
-        const uint32_t first = write(k, buf, n);
+        const uint32_t first = write(k, buf, n, (depth + 1 == L) ? T_SVO_LIST_LEAF : T_SVO_LIST);
         R_.level_nodes[k] += n / 2;
         const uint32_t leaf = (depth + 1 == L) ? valid : 0u;
         out.n = 2; out.w[0] = first; out.w[1] = valid | (leaf << 8);
@@ -443,7 +575,7 @@ class Builder {
                 if (it != map.end()) {
                     p = it->second;
                 } else {
-                    p = write(k, ch[i].w, ch[i].n);
+                    p = write(k, ch[i].w, ch[i].n, T_DAG_CHILD);
                     R_.level_nodes[k]++;
                     map.emplace(ch[i], p);
                 }
@@ -458,7 +590,7 @@ class Builder {
             if (it != map.end()) {
                 p = it->second;
             } else {
-                p = write(k, ch[i].w, ch[i].n);
+                p = write(k, ch[i].w, ch[i].n, T_DAG_CHILD);
                 R_.level_nodes[k]++;
                 map.emplace(ch[i], p);
             }
@@ -487,6 +619,7 @@ class Builder {
     int64_t corner_[3] = {0, 0, 0};
     bool cache_valid_ = false;
     int err_ = 0;
+    std::vector<WriteRec>* log_ = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -597,8 +730,10 @@ VoxelSource* make_palette_source(const uint8_t* idx, const uint32_t* palette, co
 }
 VoxelSource* make_brick_source(const vx_grid* g) { return new BrickSource(g); }
 
-int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out) {
+int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out, int threads) {
     Builder b(spec, src, dedup_scope, *out);
+    if (threads != 1 && src.thread_safe() && spec.lv.size() >= 2 && spec.lv[0].kind == K_RAW)
+        return b.run_parallel(threads > 0 ? threads : omp_get_max_threads());
     return b.run();
 }
 

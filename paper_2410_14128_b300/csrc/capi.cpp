@@ -172,7 +172,7 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
     std::unique_ptr<VoxelSource> src(grid->dense       ? make_dense_source(grid->dense, sp.ldim)
                                      : grid->dense_pal ? make_palette_source(grid->dense_pal, grid->palette, sp.ldim)
                                                        : make_brick_source(grid));
-    rc = build_canonical(sp, *src, o.dedup_scope, &V.built);
+    rc = build_canonical(sp, *src, o.dedup_scope, &V.built, o.threads);
     if (rc) return rc;
     const double t1 = now_ms();
 

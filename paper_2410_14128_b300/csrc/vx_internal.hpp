@@ -49,6 +49,8 @@ uint64_t morton_encode(const uint32_t c[3], const int e[3]);
 class VoxelSource {
   public:
     virtual ~VoxelSource() {}
+    // True when concurrent calls are safe (the parallel build needs it).
+    virtual bool thread_safe() const { return false; }
     // True only if the cube of side 2^log2s at (x0,y0,z0) holds no occupied voxel.
     virtual bool empty(int64_t x0, int64_t y0, int64_t z0, int log2s) = 0;
     // Words of the cube (side 2^log2s, corner a multiple of the side), x fastest.
@@ -69,7 +71,9 @@ struct BuildResult {
     uint64_t occupied = 0;
 };
 
-int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out);
+// threads: 1 = sequential; 0 = all cores; the parallel path needs a Raw top
+// level and a thread-safe source, and gives the same words as the sequential.
+int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out, int threads);
 
 // Device image in the packed layout (same offsets); false when the volume is
 // too large for it or has no SVDAG level (then the canonical words are used).

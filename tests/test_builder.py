@@ -186,3 +186,30 @@ def test_single_colour_dedups_strongly():
     whole = build("R(2,2,2) G(3)", g, dedup=vx.DEDUP_WHOLE_LEVEL).stats()["canonical_words"]
     per = build("R(2,2,2) G(3)", g, dedup=vx.DEDUP_PER_SUBVOLUME).stats()["canonical_words"]
     assert whole < per
+
+
+@pytest.mark.parametrize("spec", ["R(2,2,2) G(3)", "R(2,2,2) S(3)", "R(3,3,3) R(1,1,1) G(1)", "R(1,0,2) S(1) G(2)",
+                                  "R(2,2,2) S(1) R(1,1,1) G(1)"])
+@pytest.mark.parametrize("dedup", [vx.DEDUP_WHOLE_LEVEL, vx.DEDUP_PER_SUBVOLUME])
+def test_parallel_build_equals_sequential(spec, dedup):
+    (lx, ly, lz), _ = oracle.spec_dims(spec)
+    g = synth.terrain_volume(33, 1 << max(lx, ly, lz))[: 1 << lz, : 1 << ly, : 1 << lx]
+    g = np.ascontiguousarray(g)
+    seq = build(spec, g, dedup=dedup, threads=1)
+    par = build(spec, g, dedup=dedup, threads=0)
+    assert np.array_equal(seq.canonical(), par.canonical())
+    a, b = seq.stats(), par.stats()
+    for key in ("canonical_words", "occupied_voxels", "level_words", "level_nodes"):
+        assert a[key] == b[key], key
+    assert np.array_equal(oracle.decode(par.canonical(), spec), g)
+
+
+def test_parallel_build_palette_grid():
+    g8 = np.random.default_rng(5).integers(0, 4, size=(64, 64, 64)).astype(np.uint8)
+    g8[g8 == 3] = 0
+    pal = np.zeros(256, np.uint32)
+    pal[1:3] = [0xFF0000FF, 0xFF00FF00]
+    seq = vx.Volume("R(2,2,2) G(4)", g8, palette=pal, upload=False, threads=1)
+    par = vx.Volume("R(2,2,2) G(4)", g8, palette=pal, upload=False, threads=0)
+    assert np.array_equal(seq.canonical(), par.canonical())
+    assert np.array_equal(oracle.decode(par.canonical(), "R(2,2,2) G(4)"), pal[g8])
