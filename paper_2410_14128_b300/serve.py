@@ -204,8 +204,11 @@ def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.per
     results = {}
     t0 = clock()
     for req in reqs:
-        while clock() - t0 < req.arrival:
-            time.sleep(min(req.arrival - (clock() - t0), 0.001))
+        while True:
+            wait = req.arrival - (clock() - t0)
+            if wait <= 0:
+                break
+            time.sleep(min(wait, 0.001))
         start = clock() - t0
         vol = volumes[req.volume]
         hits = alloc_hits(req.n, layout)
