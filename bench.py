@@ -40,6 +40,19 @@ WORKLOAD = ("512^3 terrain (fBm heightfield + caves, RGBA8), formats R(4,4,4) S(
             "R(3,3,3) R(3,3,3) R(3,3,3); per format 1920x1080 pinhole view + 2^21 incoherent rays")
 
 
+def job_throughput(local_ms: float, rays_per_rank: int, world: int, dist=None):
+    """Whole-job throughput: every rank traced rays_per_rank rays; the job
+    took the slowest rank's time.  Returns (Mrays/s, max ms over ranks)."""
+    total_ms = local_ms
+    if dist is not None and world > 1:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * rays_per_rank / (total_ms / 1e3) / 1e6, total_ms
+
+
 def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -61,21 +74,27 @@ def kernel_src_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str):
-    """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+def ncu_counters(kernel_key: str):
+    """(DRAM bytes, warp instructions) per launch of `kernel_key` from the
+    committed ncu summary, or (None, None) when the kernel source changed
+    since it was captured."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return None, None
     sha = kernel_src_sha()
     with open(p) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
             parts = line.split()
-            if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == sha:
-                return float(parts[2])
-    return None
+            if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == sha:
+                return float(parts[2]), float(parts[3])
+    return None, None
+
+
+# Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 warp instruction per
+# cycle at the 2032 MHz maximum SM clock.
+ISSUE_PEAK_GINST_S = 148 * 4 * 2.032
 
 
 class ClockSampler:
@@ -280,24 +299,22 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    torch.cuda.nvtx.range_push("vx_timed")  # lets a profiler select the timed launches
     t_start.record()
     for s in range(args.steps):
         step(all_evs[s])
     t_end.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
+    local_ms = t_start.elapsed_time(t_end)
     for e in all_evs:
         for key, (a, b) in e.items():
             ev[key].append(a.elapsed_time(b))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = job_throughput(local_ms, rays_per_step * args.steps, world, dist)
     ms_per_step = total_ms / args.steps
-    value = world * rays_per_step * args.steps / (total_ms / 1e3) / 1e6
 
     # --- per-format results and the roofline of the dominant kernel ---
     peak, peak_kind = load_peaks()
@@ -332,12 +349,27 @@ def run_gpu(args):
     avg_ms = float(np.mean(ev[dom]))
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
     kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}"
-    traffic = ncu_traffic(kernel_key)
+    traffic, insts = ncu_counters(kernel_key)
+    if name == "render":
+        kname = "k_render"
+    else:
+        persistent = mode == vx.MODE_PERSISTENT or (mode == vx.MODE_AUTO and (not tuned or tuned[k]["mode"] == "persistent"))
+        kname = "k_trace_persistent" if persistent else "k_trace"
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"{'k_render' if name == 'render' else 'k_trace'} {FORMATS[k]}",
+                "kernel": f"{kname} {FORMATS[k]}",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    # The traversal is a chain of dependent small reads that mostly hit in L1/L2,
+    # so the unit that limits it is instruction issue: warp instructions per
+    # launch (same ncu capture) over the live launch time, against the peak.
+    roofline_issue = None
+    if insts:
+        ach = insts / (avg_ms / 1e3) / 1e9
+        roofline_issue = {"bound": "issue", "achieved": round(ach, 2), "peak": round(ISSUE_PEAK_GINST_S, 2),
+                          "unit": "Gwarp-inst/s", "frac": round(ach / ISSUE_PEAK_GINST_S, 4),
+                          "warp_inst_per_launch": insts,
+                          "peak_source": "148 SMs x 4 schedulers x 1 warp-inst/cycle x 2032 MHz (nominal)"}
 
     # --- end to end through the host-memory entry points ---
     e2e = None
@@ -393,6 +425,7 @@ def run_gpu(args):
             "plain_kernel_ms_per_step": round(plain_ms, 4) if plain_ms else None,
             "per_format": per_format,
             "roofline": roofline,
+            "roofline_issue": roofline_issue,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * len(FORMATS) * args.steps,

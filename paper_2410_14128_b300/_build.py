@@ -41,7 +41,7 @@ def _stale(src: str, obj: str, hdr_mtime: float) -> bool:
 
 def _compile(src: str, obj: str):
     if src.endswith(".cu"):
-        cmd = [NVCC, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [NVCC, *NVCC_FLAGS, *_extra_nvcc_flags(), "-c", src, "-o", obj]
     else:
         cmd = ["g++", *GXX_FLAGS, "-c", src, "-o", obj]
     p = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,6 +51,11 @@ def _compile(src: str, obj: str):
     if p.returncode != 0:
         raise RuntimeError(f"compile failed: {src}\n{p.stdout}\n{p.stderr}")
     return src
+
+
+def _extra_nvcc_flags():
+    """Extra nvcc flags from VX_NVCC_FLAGS (e.g. -DVX_CACHE_TN=0)."""
+    return os.environ.get("VX_NVCC_FLAGS", "").split()
 
 
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:

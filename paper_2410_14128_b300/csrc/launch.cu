@@ -24,7 +24,8 @@ const KernelSet g_generic = {"*",
                              &Launch<DynF>::trace_count,
                              &Launch<DynF>::trace_persistent,
                              &Launch<DynF>::trace_batch,
-                             &Launch<DynF>::resident_blocks};
+                             &Launch<DynF>::resident_blocks,
+                             &Launch<DynF>::render_persistent};
 
 CamDev to_dev(const CameraParams& c) {
     CamDev d;
@@ -189,7 +190,19 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream) {
     const int block = pick_block(o);
-    int e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block, (cudaStream_t)stream);
+    const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PLAIN;  // coherent views: plain
+    int e;
+    if (mode == VX_MODE_PERSISTENT) {
+        unsigned long long* next = v.queue_counter();
+        if (!next) return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+        const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
+        const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
+        e = v.kernels->render_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block,
+                                         refill, burst, (cudaStream_t)stream, next);
+    } else {
+        e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block,
+                              (cudaStream_t)stream);
+    }
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }

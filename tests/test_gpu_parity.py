@@ -384,3 +384,26 @@ def test_packed_device_image_equals_canonical(spec):
     a = gpu_trace(packed, rays)
     assert np.array_equal(a, gpu_trace(canon, rays))
     compare(g, rays, a)
+
+
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "S(1) G(2) R(2,2,2) S(2)"])
+def test_persistent_render_equals_plain(spec):
+    g = synth.terrain_volume(90, 128)
+    vol = vx.Volume(spec, g)
+    cam = synth.camera(91, 128, 333, 197, mode="above")
+    a, b = vx.alloc_hits(333 * 197), vx.alloc_hits(333 * 197)
+    vol.render(cam, a, mode=vx.MODE_PLAIN)
+    for refill, burst in [(8, 4), (1, 1), (32, 64)]:
+        vol.render(cam, b, mode=vx.MODE_PERSISTENT, refill=refill, burst=burst)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), (refill, burst)
+    # the fused render equals tracing its own (FP32, GPU-generated) rays ...
+    t = vx.alloc_hits(333 * 197)
+    vol.trace(vx.raygen_pinhole(cam), t, mode=vx.MODE_PLAIN)
+    torch.cuda.synchronize()
+    assert torch.equal(a, t)
+    # ... and the traversal matches the oracle on the oracle's own rays
+    prim = oracle.pinhole(cam)
+    compare(g, prim, gpu_trace(vol, prim))
+    # host variant in chunks
+    assert np.array_equal(vol.render_host(cam), vx.hits_to_numpy(a))
