@@ -41,7 +41,7 @@
  * The file also holds: the near-tie classifier, a brute-force slab checker
  * over every voxel box (tiny grids), an FP64 pinhole ray generator, and a
  * decoder of the paper's word-buffer layout (Sec. 3.3, Fig. 3) back into a
- * dense grid.
+ * dense grid, which also checks every distance a DF level stores.
  *
  * Compiled with -ffp-contract=off and no fast-math: every FP64 expression
  * below is evaluated with one IEEE rounding per operation, in source order.
@@ -467,11 +467,16 @@ void or_pinhole(const double* cam, int64_t W, int64_t H, float* rays) {
 /*         each, in child-index order (child i = x | y << 1 | z << 2).       */
 /*   SVDAG node: {masks or terminating integer, one pointer per valid        */
 /*         child}; a leaf node is one terminating-integer word.              */
+/*   DF D(W,H,D,M): a Raw grid with a second word per cell, interleaved     */
+/*         {terminating integer, l1}: cell (x,y,z) at 2 (x + (y << W) +      */
+/*         (z << (W+H))).  l1 is the L1 (Manhattan) distance, in cells, from  */
+/*         the cell to the nearest non-empty cell of the same sub-volume,    */
+/*         capped at M (0 for a non-empty cell) (Sec. 3.1, 3.3, 4.1).        */
 /* A terminating integer is a word offset of a next-level sub-volume, or the */
 /* voxel RGBA at the last level; 0 = empty.                                  */
 /* Returns 0, or a negative code: -1 bad spec, -2 pointer out of range,      */
 /* -3 inconsistent masks, -4 voxel outside the grid, -5 empty valid child,   */
-/* -6 unsupported level kind.                                                */
+/* -6 unsupported level kind, -7 a DF distance differs from its definition.  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     char kind;
@@ -603,6 +608,61 @@ static void dec_dag(dctx* C, int k, uint32_t np, int depth, int64_t lo[3]) {
     }
 }
 
+/* The distance of DF cell c: the smallest L1 distance to a non-empty cell of
+ * the sub-volume, capped at M.  Written out directly: the minimum over the
+ * list of non-empty cells, or over the cells within L1 distance M of c,
+ * whichever list is shorter (both give the definition). */
+static uint32_t df_distance(const uint32_t* cells, const int e[3], int64_t M, const int64_t* occ, int64_t nocc,
+                            int64_t cx, int64_t cy, int64_t cz) {
+    const int64_t nx = (int64_t)1 << e[0], ny = (int64_t)1 << e[1], nz = (int64_t)1 << e[2];
+    int64_t best = M;
+    const int64_t ball = (2 * M + 1) * (2 * M + 1) * (2 * M + 1);
+    if (nocc <= ball) {
+        for (int64_t q = 0; q < nocc; q++) {
+            const int64_t x = occ[q] % nx, y = (occ[q] / nx) % ny, z = occ[q] / (nx * ny);
+            const int64_t d = llabs(x - cx) + llabs(y - cy) + llabs(z - cz);
+            if (d < best) best = d;
+        }
+    } else {
+        for (int64_t dz = -M; dz <= M; dz++)
+            for (int64_t dy = -M; dy <= M; dy++)
+                for (int64_t dx = -M; dx <= M; dx++) {
+                    const int64_t d = llabs(dx) + llabs(dy) + llabs(dz);
+                    if (d >= best) continue;
+                    const int64_t x = cx + dx, y = cy + dy, z = cz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) continue;
+                    if (cells[2 * (x + nx * (y + ny * z))] != 0) best = d;
+                }
+    }
+    return (uint32_t)best;
+}
+
+static void dec_df(dctx* C, int k, uint32_t ptr, int64_t lo[3]) {
+    const dlevel* L = &C->lv[k];
+    const int64_t nx = (int64_t)1 << L->e[0], ny = (int64_t)1 << L->e[1], nz = (int64_t)1 << L->e[2];
+    const int64_t cnt = nx * ny * nz;
+    if ((uint64_t)ptr + 2ull * (uint64_t)cnt > C->nw) { C->err = -2; return; }
+    const uint32_t* cells = C->w + ptr;  /* cell i: cells[2 i] terminating integer, cells[2 i + 1] distance */
+    int64_t nocc = 0;
+    for (int64_t i = 0; i < cnt; i++) nocc += cells[2 * i] != 0;
+    int64_t* occ = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nocc > 0 ? nocc : 1));
+    nocc = 0;
+    for (int64_t i = 0; i < cnt; i++)
+        if (cells[2 * i] != 0) occ[nocc++] = i;
+    for (int64_t z = 0; z < nz && !C->err; z++)
+        for (int64_t y = 0; y < ny && !C->err; y++)
+            for (int64_t x = 0; x < nx && !C->err; x++) {
+                const int64_t i = x + nx * (y + ny * z);
+                const uint32_t w = cells[2 * i];
+                const uint32_t want = w != 0 ? 0u : df_distance(cells, L->e, L->param, occ, nocc, x, y, z);
+                if (cells[2 * i + 1] != want) { C->err = -7; break; }
+                if (w == 0) continue;
+                int64_t cl[3] = {lo[0] + (x << C->s[k][0]), lo[1] + (y << C->s[k][1]), lo[2] + (z << C->s[k][2])};
+                dec_emit(C, k, w, cl);
+            }
+    free(occ);
+}
+
 static void dec_level(dctx* C, int k, uint32_t ptr, int64_t lo[3]) {
     if (C->err) return;
     const dlevel* L = &C->lv[k];
@@ -623,6 +683,8 @@ static void dec_level(dctx* C, int k, uint32_t ptr, int64_t lo[3]) {
         dec_svo(C, k, ptr, 0, lo);
     } else if (L->kind == 'G') {
         dec_dag(C, k, ptr, 0, lo);
+    } else if (L->kind == 'D') {
+        dec_df(C, k, ptr, lo);
     } else {
         C->err = -6;
     }

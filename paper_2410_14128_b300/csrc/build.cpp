@@ -12,6 +12,10 @@
 // Layout (Sec. 3.3, Fig. 3):
 //   Raw R(W,H,D): 2^(W+H+D) terminating integers, cell (x,y,z) at
 //     x + (y << W) + (z << (W+H)).
+//   DF D(W,H,D,M): the same cells, two interleaved words each: the
+//     terminating integer and the L1 distance (in cells) to the nearest
+//     non-empty cell of the sub-volume, capped at M; computed once all the
+//     children are recorded (Sec. 4.1).
 //   SVO S(L): 2-word nodes {first-child pointer | terminating integer,
 //     valid | leaf << 8}; a node's valid children are written contiguously,
 //     2 words each, in child-index order (i = x | y << 1 | z << 2), when the
@@ -285,6 +289,7 @@ struct NodeKeyHash {
 // What a write holds, for relocating it when fragments are merged.
 enum WriteTag : uint8_t {
     T_RAW = 0,        // Raw array (pointers to level k+1 unless k is last)
+    T_DF,             // DF array {terminating integer, distance} per cell
     T_SVO_ROOT,       // SVO root node {children list, masks}
     T_DAG_ROOT,       // SVDAG root node (not de-duplicated)
     T_SVO_LIST,       // contiguous internal SVO nodes
@@ -295,6 +300,37 @@ struct WriteRec {
     uint32_t off, n;
     uint8_t tag, level;
 };
+
+// L1 distance transform of a W x H x D grid of cells, capped at M: d = 0 on
+// non-empty cells, else min(M, distance to the nearest non-empty cell).  The
+// L1 metric separates by axis, so a forward and a backward sweep along x,
+// then y, then z (each d = min(d, neighbour + 1)) give the exact distances.
+void l1_distance(const uint32_t* terms, const int e[3], uint32_t M, std::vector<uint32_t>& d) {
+    const int64_t n[3] = {(int64_t)1 << e[0], (int64_t)1 << e[1], (int64_t)1 << e[2]};
+    const int64_t stride[3] = {1, n[0], n[0] * n[1]};
+    const int64_t cells = n[0] * n[1] * n[2];
+    d.resize((size_t)cells);
+    for (int64_t i = 0; i < cells; i++) d[(size_t)i] = terms[i] ? 0u : M;
+    for (int a = 0; a < 3; a++) {
+        if (n[a] == 1) continue;
+        const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+        for (int64_t u = 0; u < n[b]; u++)
+            for (int64_t v = 0; v < n[c]; v++) {
+                uint32_t* row = d.data() + u * stride[b] + v * stride[c];
+                const int64_t st = stride[a];
+                for (int64_t i = 1; i < n[a]; i++) row[i * st] = std::min(row[i * st], row[(i - 1) * st] + 1);
+                for (int64_t i = n[a] - 2; i >= 0; i--) row[i * st] = std::min(row[i * st], row[(i + 1) * st] + 1);
+            }
+    }
+}
+
+// Interleaves terminating integers and distances into a DF sub-volume.
+void df_words(const std::vector<uint32_t>& terms, const int e[3], uint32_t M, std::vector<uint32_t>& out) {
+    std::vector<uint32_t> d;
+    l1_distance(terms.data(), e, M, d);
+    out.resize(2 * terms.size());
+    for (size_t i = 0; i < terms.size(); i++) { out[2 * i] = terms[i]; out[2 * i + 1] = d[i]; }
+}
 
 class Builder {
   public:
@@ -375,7 +411,13 @@ class Builder {
             std::vector<WriteRec>().swap(F.log);
         }
         if (any && !err_) {
-            R_.words[0] = write(0, top.data(), top.size(), T_RAW);
+            if (L0.kind == K_DF) {
+                std::vector<uint32_t> df;
+                df_words(top, L0.e, (uint32_t)L0.m, df);
+                R_.words[0] = write(0, df.data(), df.size(), T_DF);
+            } else {
+                R_.words[0] = write(0, top.data(), top.size(), T_RAW);
+            }
             R_.level_nodes[0]++;
         }
         return err_;
@@ -384,7 +426,7 @@ class Builder {
   private:
     uint8_t root_tag(int k) const {
         const int kind = sp_.lv[k].kind;
-        return kind == K_RAW ? T_RAW : (kind == K_SVO ? T_SVO_ROOT : T_DAG_ROOT);
+        return kind == K_RAW ? T_RAW : (kind == K_DF ? T_DF : (kind == K_SVO ? T_SVO_ROOT : T_DAG_ROOT));
     }
 
     uint32_t write(int k, const uint32_t* w, size_t n, uint8_t tag) {
@@ -413,6 +455,11 @@ class Builder {
                     if (!last)
                         for (uint32_t& x : tmp)
                             if (x) x = reloc[x];
+                    break;
+                case T_DF:
+                    if (!last)
+                        for (size_t i = 0; i < tmp.size(); i += 2)
+                            if (tmp[i]) tmp[i] = reloc[tmp[i]];
                     break;
                 case T_SVO_ROOT:
                 case T_SVO_LIST:
@@ -480,7 +527,7 @@ class Builder {
     bool construct(int k, const int64_t lo[3], std::vector<uint32_t>& data) {
         if (err_) return false;
         const Level& L = sp_.lv[k];
-        if (L.kind == K_RAW) {
+        if (L.kind == K_RAW || L.kind == K_DF) {
             const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
             data.assign((size_t)cells, 0u);
             bool any = false;
@@ -494,6 +541,11 @@ class Builder {
                 any |= t != 0;
             }
             if (any) R_.level_nodes[k]++;
+            if (any && L.kind == K_DF) {
+                std::vector<uint32_t> df;
+                df_words(data, L.e, (uint32_t)L.m, df);
+                data.swap(df);
+            }
             return any && !err_;
         }
         if (L.kind == K_DAG && scope_ == VX_DEDUP_PER_SUBVOLUME) {
@@ -665,15 +717,16 @@ class Decoder {
         if (err_) return;
         const Level& L = sp_.lv[k];
         const int64_t cs = (int64_t)1 << s_[k];
-        if (L.kind == K_RAW) {
+        if (L.kind == K_RAW || L.kind == K_DF) {
             const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
-            if (!in(p, cells)) return;
+            const uint64_t wpc = L.kind == K_DF ? 2 : 1;  // words per cell
+            if (!in(p, wpc * cells)) return;
             for (int64_t z = 0; z < (1 << L.e[2]); z++)
                 for (int64_t y = 0; y < (1 << L.e[1]); y++)
                     for (int64_t x = 0; x < (1 << L.e[0]); x++) {
                         const int64_t cl[3] = {lo[0] + x * cs, lo[1] + y * cs, lo[2] + z * cs};
                         if (!overlaps(cl, cs)) continue;
-                        uint32_t t = w_[p + x + (y << L.e[0]) + (z << (L.e[0] + L.e[1]))];
+                        uint32_t t = w_[p + wpc * (x + (y << L.e[0]) + (z << (L.e[0] + L.e[1])))];
                         if (t) emit(k, t, cl);
                         if (err_) return;
                     }
@@ -732,7 +785,8 @@ VoxelSource* make_brick_source(const vx_grid* g) { return new BrickSource(g); }
 
 int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out, int threads) {
     Builder b(spec, src, dedup_scope, *out);
-    if (threads != 1 && src.thread_safe() && spec.lv.size() >= 2 && spec.lv[0].kind == K_RAW)
+    if (threads != 1 && src.thread_safe() && spec.lv.size() >= 2 &&
+        (spec.lv[0].kind == K_RAW || spec.lv[0].kind == K_DF))
         return b.run_parallel(threads > 0 ? threads : omp_get_max_threads());
     return b.run();
 }

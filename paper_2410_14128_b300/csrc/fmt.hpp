@@ -2,8 +2,10 @@
 // shared by the host code and the CUDA kernels.
 //
 // A format is a list of the paper's base formats (Sec. 3.1, Table 1).  For
-// traversal every level is expanded into node levels: a Raw level R(W,H,D) is
-// one node level with 2^W x 2^H x 2^D children; an SVO or SVDAG level of
+// traversal every level is expanded into node levels: a Raw level R(W,H,D)
+// or a DF level D(W,H,D,M) is one node level with 2^W x 2^H x 2^D children
+// (a DF cell also stores its L1 distance to the nearest non-empty cell, which
+// the traversal uses to skip look-ups); an SVO or SVDAG level of
 // depth L is L node levels with 2 x 2 x 2 children each (the octree nodes of
 // Sec. 3.3).  Node level j's children are cubes of side 2^s_j voxels; all
 // levels but the first are cubic (Sec. 5), so s_j is one number per level.
@@ -22,7 +24,7 @@
 
 namespace vx {
 
-enum Kind : int { K_RAW = 0, K_SVO = 1, K_DAG = 2 };
+enum Kind : int { K_RAW = 0, K_SVO = 1, K_DAG = 2, K_DF = 3 };
 
 constexpr int kMaxFormatLevels = 16;
 constexpr int kMaxNodeLevels = 16;
@@ -42,7 +44,7 @@ struct FmtParams {
 
 struct LevelDesc {
     int kind;
-    int e[3];  // Raw: W,H,D;  SVO/SVDAG: L,L,L
+    int e[3];  // Raw / DF: W,H,D;  SVO/SVDAG: L,L,L
 };
 
 // Expands format levels into node levels.  Returns false when the format
@@ -56,12 +58,12 @@ constexpr bool make_fmt_params(const LevelDesc* lv, int n, FmtParams* out) {
     uint32_t top = 0, bot = 0;
     for (int k = 0; k < n; k++) {
         const LevelDesc& L = lv[k];
-        if (L.kind == K_RAW) {
+        if (L.kind == K_RAW || L.kind == K_DF) {
             if (L.e[0] < 0 || L.e[1] < 0 || L.e[2] < 0) return false;
             if (L.e[0] + L.e[1] + L.e[2] == 0) return false;
             if (k > 0 && (L.e[0] != L.e[1] || L.e[1] != L.e[2])) return false;
             if (J >= kMaxNodeLevels) return false;
-            kind[J] = K_RAW; bx[J] = L.e[0]; by[J] = L.e[1]; bz[J] = L.e[2];
+            kind[J] = L.kind; bx[J] = L.e[0]; by[J] = L.e[1]; bz[J] = L.e[2];
             top |= 1u << J; bot |= 1u << J;
             J++;
         } else if (L.kind == K_SVO || L.kind == K_DAG) {

@@ -8,8 +8,8 @@
 //   - a pointer to an SVDAG node p becomes (valid mask of p) << 24 | p;
 //   - an SVDAG node's slot for a leaf child holds the leaf's terminating
 //     integer itself instead of a pointer to it;
-//   - word 0 (root pointer) and Raw cells / SVO leaf words that point at an
-//     SVDAG root follow the first rule.
+//   - word 0 (root pointer) and Raw / DF cells / SVO leaf words that point
+//     at an SVDAG root follow the first rule.
 // It needs every offset below 2^24 words (64 MiB); larger volumes keep the
 // canonical words on the device (the kernels are told which layout they
 // read).
@@ -52,14 +52,15 @@ class Packer {
         seen_[p] = 1;
         const Level& L = sp_.lv[k];
         const bool last = k == nlev_ - 1;
-        if (L.kind == K_RAW) {
+        if (L.kind == K_RAW || L.kind == K_DF) {
             const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
-            if (!check(p, cells) || last) return;
+            const uint64_t wpc = L.kind == K_DF ? 2 : 1;  // DF: {terminating integer, distance}
+            if (!check(p, wpc * cells) || last) return;
             for (uint64_t i = 0; i < cells; i++) {
-                const uint32_t w = in_[p + i];
+                const uint32_t w = in_[p + wpc * i];
                 if (!w) continue;
                 level(k + 1, w);
-                out_[p + i] = ptr_for(k + 1, w);
+                out_[p + wpc * i] = ptr_for(k + 1, w);
             }
         } else if (L.kind == K_SVO) {
             svo(k, p, 0);

@@ -56,7 +56,7 @@ int parse_spec(const char* text, Spec* out) {
             long x = 0;
             while (isdigit((unsigned char)*s)) {
                 x = 10 * x + (*s++ - '0');
-                if (x > 64) return fail(VX_EINVAL, "spec '%s': extent too large", text);
+                if (x > kMaxDfCap) return fail(VX_EINVAL, "spec '%s': number too large", text);
             }
             skip();
             if (*s == '^') {
@@ -80,7 +80,11 @@ int parse_spec(const char* text, Spec* out) {
             L.e[0] = vals[0]; L.e[1] = vals[1]; L.e[2] = vals[2];
             if (L.e[0] + L.e[1] + L.e[2] == 0) return fail(VX_EINVAL, "spec '%s': R(0,0,0) holds one cell", text);
         } else if (k == 'D') {
-            return fail(VX_EUNSUPPORTED, "spec '%s': distance-field levels D(...) are not built yet", text);
+            if (nv != 4) return fail(VX_EINVAL, "spec '%s': D takes (W,H,D,M)", text);
+            L.kind = K_DF;
+            L.e[0] = vals[0]; L.e[1] = vals[1]; L.e[2] = vals[2];
+            L.m = vals[3];
+            if (L.e[0] + L.e[1] + L.e[2] == 0) return fail(VX_EINVAL, "spec '%s': D(0,0,0,M) holds one cell", text);
         } else {
             if (nv != 1 || vals[0] < 1) return fail(VX_EINVAL, "spec '%s': %c takes one depth >= 1", text, k);
             L.kind = (k == 'S') ? K_SVO : K_DAG;
@@ -100,6 +104,7 @@ int parse_spec(const char* text, Spec* out) {
         const Level& L = sp.lv[k];
         char buf[64];
         if (L.kind == K_RAW) snprintf(buf, sizeof buf, "R(%d,%d,%d)", L.e[0], L.e[1], L.e[2]);
+        else if (L.kind == K_DF) snprintf(buf, sizeof buf, "D(%d,%d,%d,%d)", L.e[0], L.e[1], L.e[2], L.m);
         else snprintf(buf, sizeof buf, "%c(%d)", L.kind == K_SVO ? 'S' : 'G', L.e[0]);
         if (k) c += ' ';
         c += buf;

@@ -25,8 +25,11 @@ void clear_error();
 // ---------------------------------------------------------------------------
 struct Level {
     int kind;  // Kind
-    int e[3];  // Raw: W,H,D; SVO/SVDAG: L,L,L
+    int e[3];  // Raw / DF: W,H,D; SVO/SVDAG: L,L,L
+    int m;     // DF: distance cap M
 };
+
+constexpr int kMaxDfCap = 65535;  // largest DF distance cap M (also bounds every number in a spec)
 
 struct Spec {
     std::vector<Level> lv;
@@ -71,8 +74,8 @@ struct BuildResult {
     uint64_t occupied = 0;
 };
 
-// threads: 1 = sequential; 0 = all cores; the parallel path needs a Raw top
-// level and a thread-safe source, and gives the same words as the sequential.
+// threads: 1 = sequential; 0 = all cores; the parallel path needs a Raw or DF
+// top level and a thread-safe source, and gives the same words as the sequential.
 int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out, int threads);
 
 // Device image in the packed layout (same offsets); false when the volume is

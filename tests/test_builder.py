@@ -47,7 +47,9 @@ def test_library_exports_every_header_function():
     ("", vx.VX_EINVAL), ("Q(3)", vx.VX_EINVAL), ("R(1,1)", vx.VX_EINVAL), ("S(0)", vx.VX_EINVAL),
     ("R(2,2,2) R(1,2,1)", vx.VX_EINVAL),            # lower levels must be cubic (Sec. 5)
     ("R(2,2,2) S(1)", vx.VX_EINVAL),                # 8^3 spec on a 16^3 grid
-    ("D(2,2,2,4) R(2,2,2)", vx.VX_EUNSUPPORTED),    # distance-field levels are not built yet
+    ("D(2,2,2) R(2,2,2)", vx.VX_EINVAL),            # D takes (W,H,D,M) (Table 1)
+    ("D(2,2,2,70000) R(2,2,2)", vx.VX_EINVAL),      # distance cap beyond the supported 65535
+    ("R(2,2,2) D(1,2,1,3)", vx.VX_EINVAL),          # lower DF levels must be cubic too (Sec. 5)
 ])
 def test_bad_specs_rejected(spec, code):
     g = np.zeros((16, 16, 16), np.uint32)
@@ -88,7 +90,9 @@ def test_builder_reproduces_hand_built_buffers(ex):
 # decode(build(G)) == G for many formats, by the oracle's decoder
 # ---------------------------------------------------------------------------
 SPECS_16 = ["R(4,4,4)", "S(4)", "G(4)", "R(2,2,2) R(2,2,2)", "R(1,1,1) S(1) G(2)", "S(2) R(2,2,2)",
-            "G(2) S(2)", "R(3,3,3) G(1)", "S(1) S(1) S(1) S(1)", "R(2,2,2) S(1) G(1)", "G(1) R(3,3,3)"]
+            "G(2) S(2)", "R(3,3,3) G(1)", "S(1) S(1) S(1) S(1)", "R(2,2,2) S(1) G(1)", "G(1) R(3,3,3)",
+            "D(4,4,4,6)", "D(2,2,2,3) R(2,2,2)", "R(2,2,2) D(2,2,2,2)", "D(1,1,1,1) S(1) G(2)",
+            "D(2,2,2,6) D(2,2,2,6)", "G(2) D(2,2,2,1)"]
 
 
 @pytest.mark.parametrize("spec", SPECS_16)
@@ -189,7 +193,7 @@ def test_single_colour_dedups_strongly():
 
 
 @pytest.mark.parametrize("spec", ["R(2,2,2) G(3)", "R(2,2,2) S(3)", "R(3,3,3) R(1,1,1) G(1)", "R(1,0,2) S(1) G(2)",
-                                  "R(2,2,2) S(1) R(1,1,1) G(1)"])
+                                  "R(2,2,2) S(1) R(1,1,1) G(1)", "D(2,2,2,6) G(3)", "D(3,1,2,4) D(2,2,2,6) R(1,1,1)"])
 @pytest.mark.parametrize("dedup", [vx.DEDUP_WHOLE_LEVEL, vx.DEDUP_PER_SUBVOLUME])
 def test_parallel_build_equals_sequential(spec, dedup):
     (lx, ly, lz), _ = oracle.spec_dims(spec)
@@ -213,3 +217,34 @@ def test_parallel_build_palette_grid():
     par = vx.Volume("R(2,2,2) G(4)", g8, palette=pal, upload=False, threads=0)
     assert np.array_equal(seq.canonical(), par.canonical())
     assert np.array_equal(oracle.decode(par.canonical(), "R(2,2,2) G(4)"), pal[g8])
+
+
+# ---------------------------------------------------------------------------
+# DF levels: distances by the oracle's definition (checked inside decode),
+# size, and the cap
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["D(5,5,5,6)", "D(3,3,3,6) R(2,2,2)", "D(2,2,2,2) D(3,3,3,6)", "R(1,1,1) D(2,2,2,9) G(2)"])
+def test_df_distances_match_definition(spec):
+    g = synth.terrain_volume(41, 32)
+    v = build(spec, g)
+    assert np.array_equal(oracle.decode(v.canonical(), spec), g)
+
+
+def test_df_words_are_twice_raw():
+    g = synth.random_grid(42, (32, 32, 32), 0.05)
+    raw = build("R(3,3,3) R(2,2,2)", g).stats()
+    df = build("D(3,3,3,6) R(2,2,2)", g).stats()
+    assert df["level_words"][0] == 2 * raw["level_words"][0]
+    assert df["level_words"][1] == raw["level_words"][1]
+    assert df["canonical_words"] == raw["canonical_words"] + raw["level_words"][0]
+
+
+def test_df_cap_closed_form():
+    # one voxel at the origin of a 16^3 D level: every cell stores min(x + y + z, M)
+    g = np.zeros((16, 16, 16), np.uint32)
+    g[0, 0, 0] = 0xFF0000FF
+    for M in (0, 1, 5, 45, 65535):
+        w = build(f"D(4,4,4,{M})", g).canonical()
+        d = w[1 + 1::2][: 16 ** 3].reshape(16, 16, 16)
+        z, y, x = np.indices((16, 16, 16))
+        assert np.array_equal(d, np.minimum(x + y + z, M)), M
