@@ -502,12 +502,25 @@ def run_sweep(args):
         ms_prim = _timed(torch, lambda: [v.render(c, h) for c, h in zip(cams, hits)], args.steps, args.warmup)
         ms_ao = _timed(torch, lambda: v.trace(ao, ao_hits), args.steps, args.warmup)
         n_ao_live = int((ao[:, 7] > 0).sum().item())
+        # node stack vs restarting traversal (Sec. 4.4) on the same rays
+        prim = torch.cat(rays)
+        prim_hits = vx.alloc_hits(prim.shape[0])
+        trav = {}
+        for rs in (False, True):
+            mp = _timed(torch, lambda: v.trace(prim, prim_hits, mode=vx.MODE_PLAIN, restart=rs), args.steps,
+                        args.warmup)
+            ma = _timed(torch, lambda: v.trace(ao, ao_hits, mode=vx.MODE_PERSISTENT, restart=rs), args.steps,
+                        args.warmup)
+            trav["restart" if rs else "stack"] = {"mrays_s_primary_plain": round(prim.shape[0] / mp / 1e3, 1),
+                                                  "mrays_s_ao_persistent": round(ao.shape[0] / ma / 1e3, 1)}
+        del prim, prim_hits
         per.append({"format": spec, "build_s": round(build_s, 1), "device_bytes": st["device_bytes"],
                     "bytes_per_voxel": round(st["device_bytes"] / 2048 ** 3, 6),
                     "bytes_per_occupied_voxel": round(st["device_bytes"] / max(1, st["occupied_voxels"]), 4),
                     "mrays_s_primary": round(len(cams) * n_prim / ms_prim / 1e3, 1),
                     "mrays_s_ao": round(ao.shape[0] / ms_ao / 1e3, 1), "ao_rays": int(ao.shape[0]),
-                    "ao_rays_live": n_ao_live, "specialized_kernel": st["specialized"], "tuned": tune})
+                    "ao_rays_live": n_ao_live, "specialized_kernel": st["specialized"], "tuned": tune,
+                    "traversal": trav})
         del hits, rays, ao, ao_hits
         v.free()
         torch.cuda.empty_cache()

@@ -213,7 +213,14 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *          side 2^g) for coherence; hits still land in the caller's order.
  *          Sorting takes 8 B per ray plus up to 1 MiB of device scratch from
  *          CUDA's stream-ordered allocator (cudaMallocAsync), at most 2^32 - 1
- *          rays per call.
+ *          rays per call;
+ *   restart 0 = octree levels keep a per-ray stack of the nodes entered;
+ *          1 = restarting sparse-voxel intersection (Sec. 4.4): keep only
+ *          each format level's root and walk an SVO / SVDAG level again from
+ *          its root after leaving one of its nodes (same results, no stack
+ *          per octree depth, redundant node reads).  Used by vx_trace and
+ *          vx_trace_counted; vx_render, vx_trace_batch and vx_trace_noalloc
+ *          always keep the stack.  Any other value: VX_EINVAL.
  * Persistent launches take a queue counter from a ring of 256 per volume, so
  * up to 256 of them may be in flight at once per volume. */
 typedef struct vx_trace_opts {
@@ -224,7 +231,7 @@ typedef struct vx_trace_opts {
     int32_t refill;
     int32_t burst;
     int32_t sort_cell_log2;
-    int32_t reserved;
+    int32_t restart;
 } vx_trace_opts;
 
 /* First hit of each ray (Sec. 4.2: the root function reads the root pointer,

@@ -64,7 +64,7 @@ class _Stats(ctypes.Structure):
 class _TraceOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
-                ("sort_cell_log2", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sort_cell_log2", ctypes.c_int32), ("restart", ctypes.c_int32)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -138,10 +138,11 @@ def _check(rc: int):
         raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
 
 
-def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0):
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False):
     o = _TraceOpts()
     o.mode, o.block, o.blocks_per_sm, o.smem_top, o.refill, o.burst = mode, block, blocks_per_sm, 0, refill, burst
     o.sort_cell_log2 = sort
+    o.restart = int(restart)
     return o
 
 
@@ -310,7 +311,8 @@ class Volume:
         _check(lib().vx_autotune(self._h, ctypes.c_void_p(sample_rays.data_ptr()), sample_rays.shape[0],
                                  _stream_handle(stream), ctypes.byref(o), ctypes.byref(ms)))
         return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
-                "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "sample_ms": ms.value}
+                "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
+                "sample_ms": ms.value}
 
     def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,
                    **opts) -> np.ndarray:

@@ -69,6 +69,7 @@ int check_opts(const vx_trace_opts* o) {
         return fail(VX_EINVAL, "sort_cell_log2 must be in [0, 15], got %d", o->sort_cell_log2);
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
         return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
+    if (o->restart != 0 && o->restart != 1) return fail(VX_EINVAL, "restart must be 0 or 1, got %d", o->restart);
     return VX_OK;
 }
 
@@ -379,6 +380,11 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
         rc = time_opts(V, rays, n, hits, cand, st, a, b, &ms);
         if (!rc && ms < cur_ms) { cur = cand; cur_ms = ms; }
     };
+    // restarting traversal differs from the stack only below an octree
+    // level's root, i.e. for SVO / SVDAG levels of depth 2 or more
+    bool deep_octree = false;
+    for (const Level& L : V.spec.lv) deep_octree |= (L.kind == K_SVO || L.kind == K_DAG) && L.e[0] >= 2;
+    if (deep_octree) { vx_trace_opts c = cur; c.restart = 1; consider(c); }
     const int maxg = std::min(V.spec.ldim[0], std::min(V.spec.ldim[1], V.spec.ldim[2]));
     for (int g : {2, 3, 4, 5, 6, 7}) {
         if (g > maxg) break;

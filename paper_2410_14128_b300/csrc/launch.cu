@@ -144,6 +144,7 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     const int block = pick_block(o);
     const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PERSISTENT;
     const int sort = o ? o->sort_cell_log2 : 0;
+    const int restart = o ? o->restart : 0;
     cudaStream_t st = (cudaStream_t)stream;
     // Optional coherence sort: scratch from the stream-ordered pool, freed
     // on the same stream after the trace.
@@ -168,10 +169,10 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
         e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits,
-                                        layout, block, bps, refill, burst, st, next);
+                                        layout, block, bps, refill, burst, restart, st, next);
     } else {
         e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
-                             block, st);
+                             block, restart, st);
     }
     if (scratch) cudaFreeAsync(scratch, st);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -181,8 +182,9 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
 int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout,
                        const vx_trace_opts* o, void* stream, unsigned long long* counters) {
     const int block = pick_block(o);
+    const int restart = o ? o->restart : 0;
     int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), n, hits, layout,
-                                   block, (cudaStream_t)stream, counters);
+                                   block, restart, (cudaStream_t)stream, counters);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }
@@ -293,7 +295,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
     for (int i = 0; i < nsub; i++) {
         Sub& g = subs[i];
         int per_sm = 1;
-        int rc = g.ks->resident_blocks(layout, block, &per_sm);
+        int rc = g.ks->resident_blocks(g.v0->spec.fmt, layout, block, &per_sm);
         if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
         // Every launch gets a full GPU's worth of resident blocks: the
         // launches run one after another in effect, each draining its queue

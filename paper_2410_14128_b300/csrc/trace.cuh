@@ -58,15 +58,17 @@ struct DynF {
     __device__ __forceinline__ int s(int j) const { return (int)((p.s >> (4 * j)) & 15u); }
     __device__ __forceinline__ int b(int j) const { return (int)((p.b >> (4 * j)) & 15u); }
     __device__ __forceinline__ bool bot(int j) const { return (p.bot >> j) & 1u; }
+    __device__ __forceinline__ uint32_t top() const { return p.top; }
     __device__ __forceinline__ int b0(int a) const { return (int)p.b0[a]; }
     __device__ __forceinline__ int ldim(int a) const { return (int)p.ldim[a]; }
     __device__ __forceinline__ int jpop(int h) const { return (int)((p.jpop >> (4 * h)) & 15u); }
     __device__ __forceinline__ bool has_svo() const { return true; }
     __device__ __forceinline__ bool has_dag() const { return true; }
+    __device__ __forceinline__ bool has_df() const { return true; }
 };
 
 template <uint32_t J_, uint32_t KIND, uint32_t BOT, uint64_t S, uint64_t B, uint32_t B0X, uint32_t B0Y, uint32_t B0Z,
-          uint32_t LX, uint32_t LY, uint32_t LZ, uint64_t JPOP>
+          uint32_t LX, uint32_t LY, uint32_t LZ, uint64_t JPOP, uint32_t TOP>
 struct StatF {
     static constexpr int kMaxJ = (int)J_;
     __device__ __forceinline__ int J() const { return (int)J_; }
@@ -74,19 +76,28 @@ struct StatF {
     __device__ __forceinline__ int s(int j) const { return (int)((S >> (4 * j)) & 15u); }
     __device__ __forceinline__ int b(int j) const { return (int)((B >> (4 * j)) & 15u); }
     __device__ __forceinline__ bool bot(int j) const { return (BOT >> j) & 1u; }
+    __device__ __forceinline__ uint32_t top() const { return TOP; }
     __device__ __forceinline__ int b0(int a) const { return (int)(a == 0 ? B0X : (a == 1 ? B0Y : B0Z)); }
     __device__ __forceinline__ int ldim(int a) const { return (int)(a == 0 ? LX : (a == 1 ? LY : LZ)); }
     __device__ __forceinline__ int jpop(int h) const { return (int)((JPOP >> (4 * h)) & 15u); }
     static constexpr bool kHasSvo = (KIND & 0x55555555u & ~(KIND >> 1)) != 0;
     static constexpr bool kHasDag = ((KIND >> 1) & 0x55555555u & ~KIND) != 0;
+    static constexpr bool kHasDf = (KIND & (KIND >> 1) & 0x55555555u) != 0;
     __device__ __forceinline__ bool has_svo() const { return kHasSvo; }
     __device__ __forceinline__ bool has_dag() const { return kHasDag; }
+    __device__ __forceinline__ bool has_df() const { return kHasDf; }
 };
 
 // Compile-time composition: Format<Raw<4,4,4>, Svo<2>, Dag<3>>.
 template <int W, int H, int D>
 struct Raw {
     static constexpr LevelDesc desc() { return LevelDesc{K_RAW, {W, H, D}}; }
+};
+// D(W,H,D,M): the cap M is a property of the stored distances, not of the
+// traversal, so the kernel does not depend on it.
+template <int W, int H, int D, int M>
+struct Df {
+    static constexpr LevelDesc desc() { return LevelDesc{K_DF, {W, H, D}}; }
 };
 template <int L>
 struct Svo {
@@ -107,7 +118,8 @@ struct Format {
     }
     static constexpr FmtParams P = make();
     static_assert(P.J > 0, "format cannot be composed");
-    using F = StatF<P.J, P.kind, P.bot, P.s, P.b, P.b0[0], P.b0[1], P.b0[2], P.ldim[0], P.ldim[1], P.ldim[2], P.jpop>;
+    using F = StatF<P.J, P.kind, P.bot, P.s, P.b, P.b0[0], P.b0[1], P.b0[2], P.ldim[0], P.ldim[1], P.ldim[2], P.jpop,
+                    P.top>;
 };
 
 // ---------------------------------------------------------------------------
@@ -261,7 +273,18 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // pop).  Both return true once the ray is finished, with the record in `out`.
 // Keeping the state between calls lets a warp swap finished rays for new ones
 // without leaving the loop (persistent kernels).
-template <bool COUNT, class F>
+//
+// The node stack (pointer and valid mask of the node entered at each node
+// level) lives in shared memory, entry j of thread t at S[j * blockDim + t]:
+// lanes touch consecutive words whatever level each is at, so accesses are
+// free of bank conflicts, and the stack never competes with node reads for
+// L1 lines as a local-memory stack does.
+//
+// RESTART selects the paper's restarting sparse-voxel intersection (Sec.
+// 4.4): only the root node of each format level is kept; leaving a node of
+// an SVO or SVDAG level walks that level's octree again from its root down
+// to the resuming node level, at the price of re-reading those nodes.
+template <bool COUNT, class F, bool RESTART = false>
 struct Walker {
     RayIn r;
     float inv[3];
@@ -271,12 +294,13 @@ struct Walker {
     int sg[3];
     int v0[3], c[3];
     int j, la, lp, budget;
+    int skip;  // DF level: cells the walk may still enter without a look-up
     int kind_c, s_c, b_c[3];  // node level j: kind, children side, fanout (cached)
     bool bot_c;
     bool fresh;
-    uint32_t Pc, Mc;  // node of level j (also kept in P[j], M[j])
-    uint32_t* P;      // per-level node stack, F::kMaxJ entries each, owned by
-    uint32_t* M;      // the caller (kept outside so the scalars stay in registers)
+    uint32_t Pc, Mc;  // node of level j: pointer, valid mask
+    uint2* S;         // this thread's node stack: entry j at S[j * ss]
+    int ss;           // stack stride (threads of the block)
     Cnt cnt;
 
     __device__ __forceinline__ void load_level(const F& f) {
@@ -285,6 +309,37 @@ struct Walker {
         bot_c = f.bot(j);
         if (j == 0) { b_c[0] = f.b0(0); b_c[1] = f.b0(1); b_c[2] = f.b0(2); }
         else { b_c[0] = b_c[1] = b_c[2] = f.b(j); }
+    }
+
+    // Node of level j reached from the root of its format level: the nodes
+    // on the way are ancestors of the cell the walk just left, so each exists.
+    // Node level d's child holding cell c (side 2^s_j) has index bit
+    // (c >> (s_d - s_j)) & 1 per axis.
+    __device__ __forceinline__ void restart(const F& f, const Img im) {
+        const uint32_t* __restrict__ pool = im.w;
+        const int r = 31 - __clz(f.top() & ((2u << j) - 1u));
+        const uint2 e = S[r * ss];
+        uint32_t p = e.x, m = e.y;
+        const bool svo = f.has_svo() && f.kind(r) == K_SVO;
+        const int sj = f.s(j);
+        for (int d = r; d < j; d++) {
+            const int sh = f.s(d) - sj;
+            const uint32_t idx = ((uint32_t)(c[0] >> sh) & 1u) | (((uint32_t)(c[1] >> sh) & 1u) << 1) |
+                                 (((uint32_t)(c[2] >> sh) & 1u) << 2);
+            const uint32_t rank = __popc(m & ((1u << idx) - 1u));
+            if (svo) {
+                const uint32_t a = p + 2u * rank;
+                p = ldw(pool, a);
+                m = ldw(pool, a + 1) & 0xFFu;
+                VX_CNT(bytes, 8);
+            } else {
+                const uint32_t cp = ldw(pool, p + 1u + rank);
+                if (im.packed) { p = cp & kPtrMask; m = cp >> 24; VX_CNT(bytes, 4); }
+                else { p = cp; m = ldw(pool, cp) & 0xFFu; VX_CNT(bytes, 8); }
+            }
+        }
+        Pc = p;
+        Mc = m;
     }
 
     // |x - y| within the guard band (true for NaN: decide in FP64)
@@ -388,14 +443,13 @@ struct Walker {
         }
         {
             const int k0 = f.kind(0);
-            if (k0 == K_RAW) { P[0] = root; M[0] = 0; }
-            else if (k0 == K_SVO) { P[0] = ldw(pool, root); M[0] = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
-            else if (im.packed) { P[0] = root & kPtrMask; M[0] = root >> 24; }
-            else { P[0] = root; M[0] = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
+            if (k0 == K_RAW || k0 == K_DF) { Pc = root; Mc = 0; }
+            else if (k0 == K_SVO) { Pc = ldw(pool, root); Mc = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+            else if (im.packed) { Pc = root & kPtrMask; Mc = root >> 24; }
+            else { Pc = root; Mc = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
         }
         j = 0;
-        Pc = P[0];
-        Mc = M[0];
+        S[0] = make_uint2(Pc, Mc);
         {
             const int s0 = f.s(0);
 #pragma unroll
@@ -417,6 +471,7 @@ struct Walker {
         // costs at most J descents; past this bound the ray reports ST_ERROR.
         budget = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (f.J() + 2);
         load_level(f);
+        skip = 0;
         return false;
     }
 
@@ -443,6 +498,24 @@ struct Walker {
             w = ldw(pool, Pc + idx);
             VX_CNT(bytes, 4);
             occ = w != 0u;
+        } else if (f.has_df() && kind == K_DF) {
+            // DF cell {terminating integer, L1 distance d}: every cell within
+            // L1 distance d - 1 is empty, and each Amanatides-Woo step moves
+            // one cell along one axis, so the next d - 1 cells of the walk at
+            // this level are entered without reading them (Sec. 4.2).
+            if (skip > 0) {
+                --skip;
+                occ = false;
+            } else {
+                const uint32_t a = Pc + 2u * idx;
+                w = ldw(pool, a);
+                VX_CNT(bytes, 4);
+                occ = w != 0u;
+                if (!occ) {
+                    skip = (int)ldw(pool, a + 1) - 1;
+                    VX_CNT(bytes, 4);
+                }
+            }
         } else {
             occ = (Mc >> idx) & 1u;
         }
@@ -450,7 +523,7 @@ struct Walker {
             // ---- descend (or hit at the last node level) ----
             uint32_t term = w, Pn = 0, Mn = 0;
             bool node_ready = false;
-            if (kind != K_RAW) {
+            if (kind == K_SVO || kind == K_DAG) {
                 const uint32_t rank = __popc(Mc & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = Pc + 2u * rank;
@@ -479,14 +552,13 @@ struct Walker {
             }
             if (!node_ready) {
                 const int nk = f.kind(j + 1);
-                if (nk == K_RAW) { Pn = term; }
+                if (nk == K_RAW || nk == K_DF) { Pn = term; }
                 else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
                 else if (im.packed) { Pn = term & kPtrMask; Mn = term >> 24; }
                 else { Pn = term; Mn = ldw(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
-            P[j] = Pn;
-            M[j] = Mn;
+            if (!RESTART || ((f.top() >> j) & 1u)) S[j * ss] = make_uint2(Pn, Mn);
             Pc = Pn;
             Mc = Mn;
             load_level(f);
@@ -568,6 +640,7 @@ struct Walker {
         const int h = 31 - __clz((uint32_t)(old ^ nw)) + s;  // highest changed voxel-coordinate bit
         const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
         if (h >= span) {
+            skip = 0;  // the distances are those of the node the walk left
             if (h >= f.ldim(a)) {
                 out = miss_rec(ST_MISS);
                 return true;
@@ -577,8 +650,13 @@ struct Walker {
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] >>= sh;
             j = jp;
-            Pc = P[j];
-            Mc = M[j];
+            if (RESTART) {
+                restart(f, im);
+            } else {
+                const uint2 e = S[j * ss];
+                Pc = e.x;
+                Mc = e.y;
+            }
             load_level(f);
         }
         return false;
@@ -586,12 +664,24 @@ struct Walker {
 };
 #undef VX_CNT
 
-template <bool COUNT, class F>
+// Dynamic shared memory of every walker kernel: the node stacks of its
+// threads, stack_bytes(J, block) bytes.
+extern __shared__ uint2 vx_stack_smem[];
+
+__host__ __device__ __forceinline__ size_t stack_bytes(uint32_t J, int block) {
+    return (size_t)J * (size_t)block * sizeof(uint2);
+}
+
+template <class Wk>
+__device__ __forceinline__ void bind_stack(Wk& w) {
+    w.S = vx_stack_smem + threadIdx.x;
+    w.ss = (int)blockDim.x;
+}
+
+template <bool COUNT, class F, bool RESTART = false>
 __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt) {
-    uint32_t P[F::kMaxJ], M[F::kMaxJ];
-    Walker<COUNT, F> w;
-    w.P = P;
-    w.M = M;
+    Walker<COUNT, F, RESTART> w;
+    bind_stack(w);
     HitRec h;
     if (!w.start(f, pool, r, h))
         while (!w.step(f, pool, h)) {
@@ -664,7 +754,7 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // ---------------------------------------------------------------------------
 // `order` (optional): launch slot k traces ray order[k] and writes its hit
 // at order[k] (rays sorted for coherence, results in the caller's order).
-template <class F, int LAYOUT>
+template <class F, int LAYOUT, bool RS = false>
 __global__ void __launch_bounds__(256) k_trace(F f, const Img pool, const float4* __restrict__ rays,
                                                const uint32_t* __restrict__ order, uint64_t n,
                                                void* __restrict__ hits) {
@@ -673,14 +763,14 @@ __global__ void __launch_bounds__(256) k_trace(F f, const Img pool, const float4
     const uint64_t i = order ? (uint64_t)__ldg(order + k) : k;
     const RayIn r = load_ray(rays, i);
     Cnt cnt;
-    const HitRec h = trace_ray<false>(f, pool, r, cnt);
+    const HitRec h = trace_ray<false, F, RS>(f, pool, r, cnt);
     store_hit<LAYOUT>(f, hits, i, h);
 }
 
 // Instrumented twin of k_trace: same results, plus totals of the per-ray
 // counters in counters[0..2] (bytes of the format read, iterations, FP64
 // decisions), summed per warp then added atomically.
-template <class F, int LAYOUT>
+template <class F, int LAYOUT, bool RS = false>
 __global__ void __launch_bounds__(256) k_trace_count(F f, const Img pool,
                                                      const float4* __restrict__ rays, uint64_t n,
                                                      void* __restrict__ hits, unsigned long long* counters) {
@@ -688,7 +778,7 @@ __global__ void __launch_bounds__(256) k_trace_count(F f, const Img pool,
     Cnt cnt;
     if (i < n) {
         const RayIn r = load_ray(rays, i);
-        const HitRec h = trace_ray<true>(f, pool, r, cnt);
+        const HitRec h = trace_ray<true, F, RS>(f, pool, r, cnt);
         store_hit<LAYOUT>(f, hits, i, h);
     }
     unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64;
@@ -712,10 +802,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
                                                            unsigned long long* next, int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t P[F::kMaxJ], M[F::kMaxJ];
     Walker<false, F> w;
-    w.P = P;
-    w.M = M;
+    bind_stack(w);
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t slot = 0;
@@ -761,7 +849,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // the idle lanes in lane order (ballot + popc rank + shuffle); busy lanes keep
 // walking.  Each round advances every live lane by up to `burst` iterations.
 // `next` must be zero at launch; the kernel leaves it >= n.
-template <class F, int LAYOUT>
+template <class F, int LAYOUT, bool RS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
                                                           const uint32_t* __restrict__ order, uint64_t n,
@@ -769,10 +857,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
                                                           int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t P[F::kMaxJ], M[F::kMaxJ];
-    Walker<false, F> w;
-    w.P = P;
-    w.M = M;
+    Walker<false, F, RS> w;
+    bind_stack(w);
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -830,10 +916,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t n = desc.start[desc.count];
-    uint32_t P[F::kMaxJ], M[F::kMaxJ];
     Walker<false, F> w;
-    w.P = P;
-    w.M = M;
+    bind_stack(w);
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -904,18 +988,18 @@ struct KernelSet {
     bool specialized;
     FmtParams params;
     int (*trace)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
-                 void* hits, int layout, int block, cudaStream_t st);
+                 void* hits, int layout, int block, int restart, cudaStream_t st);
     int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
-                       int layout, int block, cudaStream_t st, unsigned long long* counters);
+                       int layout, int block, int restart, cudaStream_t st, unsigned long long* counters);
     int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
-                            cudaStream_t st, unsigned long long* next);
+                            int restart, cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
     int (*trace_batch)(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill, int burst,
                        cudaStream_t st, unsigned long long* next);
-    int (*resident_blocks)(int layout, int block, int* per_sm);
+    int (*resident_blocks)(const FmtParams& p, int layout, int block, int* per_sm);
     int (*render_persistent)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
                              void* hits, int layout, int block, int refill, int burst, cudaStream_t st,
                              unsigned long long* next);
@@ -925,37 +1009,50 @@ template <class F>
 struct Launch {
     static F make(const FmtParams& p);
     static int trace(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
-                     void* hits, int layout, int block, cudaStream_t st) {
+                     void* hits, int layout, int block, int restart, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0) k_trace<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
-        else k_trace<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        const size_t sm = stack_bytes(p.J, block);
+        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else k_trace<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
         return (int)cudaGetLastError();
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
-                           int layout, int block, cudaStream_t st, unsigned long long* counters) {
+                           int layout, int block, int restart, cudaStream_t st, unsigned long long* counters) {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0) k_trace_count<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
-        else k_trace_count<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+        const size_t sm = stack_bytes(p.J, block);
+        if (layout == 0 && !restart)
+            k_trace_count<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+        else if (layout == 0)
+            k_trace_count<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+        else if (!restart)
+            k_trace_count<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+        else
+            k_trace_count<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
     static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
-                                int burst, cudaStream_t st, unsigned long long* next) {
+                                int burst, int restart, cudaStream_t st, unsigned long long* next) {
         if (n == 0) return 0;
         const F f = make(p);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t sm = stack_bytes(p.J, block);
         int per_sm = blocks_per_sm;
         if (per_sm <= 0) {
-            cudaError_t e = layout == 0
-                                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0>, block, 0)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1>, block, 0);
+            cudaError_t e;
+            if (layout == 0 && !restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, false>, block, sm);
+            else if (layout == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, true>, block, sm);
+            else if (!restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, false>, block, sm);
+            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, true>, block, sm);
             if (e) return (int)e;
             if (per_sm < 1) per_sm = 1;
         }
@@ -964,28 +1061,33 @@ struct Launch {
         if (grid > need) grid = need;
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
-        if (layout == 0)
-            k_trace_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill,
-                                                                        burst);
+        const unsigned g = (unsigned)grid;
+        if (layout == 0 && !restart)
+            k_trace_persistent<F, 0, false><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+        else if (layout == 0)
+            k_trace_persistent<F, 0, true><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+        else if (!restart)
+            k_trace_persistent<F, 1, false><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         else
-            k_trace_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill,
-                                                                        burst);
+            k_trace_persistent<F, 1, true><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
-    static int resident_blocks(int layout, int block, int* per_sm) {
+    static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
+        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, 0);
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, sm)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, sm);
         if (*per_sm < 1) *per_sm = 1;
         return (int)e;
     }
     static int trace_batch(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill,
                            int burst, cudaStream_t st, unsigned long long* next) {
         const F f = make(p);
+        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
-        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
-        else k_trace_batch<F, 1><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
+        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
+        else k_trace_batch<F, 1><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render_persistent(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -996,9 +1098,10 @@ struct Launch {
         int dev = 0, sms = 0, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, 0);
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, sm)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, sm);
         if (e) return (int)e;
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)sms * per_sm;
@@ -1007,9 +1110,9 @@ struct Launch {
         e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         if (layout == 0)
-            k_render_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         else
-            k_render_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -1017,8 +1120,9 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
-        else k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
+        const size_t sm = stack_bytes(p.J, block);
+        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits);
+        else k_render<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits);
         return (int)cudaGetLastError();
     }
 };

@@ -162,7 +162,8 @@ def terrain512():
     return synth.terrain_volume(2024, 512)
 
 
-@pytest.mark.parametrize("spec", ["R(4,4,4) S(2) G(3)", "R(3,3,3) R(3,3,3) R(3,3,3)"])
+@pytest.mark.parametrize("spec", ["R(4,4,4) S(2) G(3)", "R(3,3,3) R(3,3,3) R(3,3,3)",
+                                  "D(3,3,3,6) D(3,3,3,6) G(3)", "D(4,4,4,6) G(5)", "D(5,5,5,6) D(4,4,4,6)"])
 def test_terrain512_full_size_sampled(terrain512, spec):
     g = terrain512
     vol = vx.Volume(spec, g)
@@ -407,3 +408,109 @@ def test_persistent_render_equals_plain(spec):
     compare(g, prim, gpu_trace(vol, prim))
     # host variant in chunks
     assert np.array_equal(vol.render_host(cam), vx.hits_to_numpy(a))
+
+
+# ---------------------------------------------------------------------------
+# Restarting sparse-voxel intersection (Sec. 4.4): same hits as the stack,
+# more node reads
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["G(7)", "S(7)", "R(3,3,3) S(2) G(2)", "S(1) G(2) R(2,2,2) S(2)", "R(1,1,1) S(3) G(3)"])
+@pytest.mark.parametrize("canonical", [False, True])
+def test_restart_equals_stack(spec, canonical):
+    g = synth.terrain_volume(91, 128)
+    rays = np.concatenate([synth.incoherent_rays(92, 128, 60001), synth.box_rays(93, 128, 40, 20000),
+                           lattice_rays(94, (128, 128, 128), 5000)])
+    vol = vx.Volume(spec, g, canonical_device=canonical)
+    stack = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    compare(g, rays, stack)
+    for mode in (vx.MODE_PLAIN, vx.MODE_PERSISTENT):
+        for block in (64, 256):
+            got = gpu_trace(vol, rays, mode=mode, block=block, restart=True)
+            assert np.array_equal(got, stack), (mode, block)
+    # the instrumented kernel sees the redundant reads
+    r = torch.from_numpy(rays).cuda()
+    counts = []
+    for restart in (False, True):
+        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        h = vx.alloc_hits(len(rays))
+        vol.trace_counted(r, h, c, restart=restart)
+        torch.cuda.synchronize()
+        assert np.array_equal(vx.hits_to_numpy(h), stack)
+        counts.append([int(x) for x in c.cpu()])
+    assert counts[1][0] > counts[0][0]   # bytes read
+    assert counts[1][1] == counts[0][1]  # same loop iterations
+    assert counts[1][2] == counts[0][2]  # same FP64 decisions
+
+
+def test_restart_small_grids_and_bad_value():
+    for spec in ["S(4)", "G(4)", "G(2) S(2)", "R(1,1,1) S(1) G(2)"]:
+        g = synth.random_grid(hash(spec) & 0xFFFF, (16, 16, 16), 0.1, colors=3)
+        rays = np.concatenate([ranged(synth.box_rays(95, 16, 6, 20000), 96), lattice_rays(97, (16, 16, 16), 20000)])
+        vol = vx.Volume(spec, g)
+        compare(g, rays, gpu_trace(vol, rays, restart=True, mode=vx.MODE_PLAIN))
+        compare(g, rays, gpu_trace(vol, rays, restart=True, mode=vx.MODE_PERSISTENT))
+    with pytest.raises(vx.VxError):
+        gpu_trace(vol, rays, restart=2)
+
+
+# ---------------------------------------------------------------------------
+# DF levels D(W,H,D,M): skipping by the stored distance changes neither the
+# hits nor the cells walked
+# ---------------------------------------------------------------------------
+DF_SPECS_16 = ["D(4,4,4,6)", "D(2,2,2,3) R(2,2,2)", "R(2,2,2) D(2,2,2,2)", "D(1,1,1,1) S(1) G(2)",
+               "D(2,2,2,6) D(2,2,2,6)", "G(2) D(2,2,2,1)", "D(4,4,4,0)"]
+
+
+@pytest.mark.parametrize("spec", DF_SPECS_16)
+@pytest.mark.parametrize("p", [0.01, 0.2])
+def test_df_small_grids_adversarial(spec, p):
+    g = synth.random_grid(hash((spec, p, "df")) & 0xFFFF, (16, 16, 16), p, colors=4)
+    dims = (16, 16, 16)
+    rays = np.concatenate([
+        ranged(synth.box_rays(17, 16, 6, 20000), 18),
+        ranged(synth.aimed_rays(19, dims, 20000), 20),
+        lattice_rays(21, dims, 20000),
+    ])
+    vol = vx.Volume(spec, g)
+    res = compare(g, rays, gpu_trace(vol, rays))
+    assert res["hits"] > 500
+    assert np.array_equal(gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT), gpu_trace(vol, rays, mode=vx.MODE_PLAIN))
+
+
+@pytest.mark.parametrize("df,raw", [("D(3,3,3,6) R(3,3,3) G(1)", "R(3,3,3) R(3,3,3) G(1)"),
+                                    ("D(2,2,2,6) D(3,3,3,6) G(2)", "R(2,2,2) R(3,3,3) G(2)"),
+                                    ("D(4,4,4,6) G(3)", "R(4,4,4) G(3)"),
+                                    ("S(2) D(3,3,3,3) R(2,2,2)", "S(2) R(3,3,3) R(2,2,2)")])
+def test_df_walks_the_same_cells_as_raw(df, raw):
+    g = synth.terrain_volume(111, 128)
+    rays = np.concatenate([synth.incoherent_rays(112, 128, 60001), synth.box_rays(113, 128, 40, 20000)])
+    r = torch.from_numpy(rays).cuda()
+    out = {}
+    for spec in (df, raw):
+        vol = vx.Volume(spec, g)
+        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        h = vx.alloc_hits(len(rays))
+        vol.trace_counted(r, h, c)
+        torch.cuda.synchronize()
+        out[spec] = (vx.hits_to_numpy(h), [int(x) for x in c.cpu()])
+    compare(g, rays, out[df][0])
+    assert np.array_equal(out[df][0], out[raw][0])
+    assert out[df][1][1] == out[raw][1][1]  # same loop iterations: every cell is still entered
+    assert out[df][1][2] == out[raw][1][2]  # same FP64 decisions
+
+
+@pytest.mark.parametrize("spec", ["D(3,3,3,6) G(4)", "D(2,2,2,6) S(3) G(2)"])
+def test_df_packed_restart_persistent(spec):
+    g = synth.terrain_volume(114, 128)
+    rays = np.concatenate([synth.incoherent_rays(115, 128, 50001), lattice_rays(116, (128, 128, 128), 5000)])
+    ref = None
+    for canonical in (False, True):
+        vol = vx.Volume(spec, g, canonical_device=canonical)
+        assert vol.stats()["packed"] == (not canonical)
+        for mode in (vx.MODE_PLAIN, vx.MODE_PERSISTENT):
+            for restart in (False, True):
+                got = gpu_trace(vol, rays, mode=mode, restart=restart)
+                if ref is None:
+                    ref = got
+                    compare(g, rays, ref)
+                assert np.array_equal(got, ref), (canonical, mode, restart)
