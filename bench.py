@@ -442,9 +442,21 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # Other workloads (one JSON line each; the default line is the 512^3 one)
 # ---------------------------------------------------------------------------
-SWEEP_FORMATS = ["R(4,4,4) R(3,3,3) G(4)", "R(4,4,4) S(3) G(4)", "R(4,4,4) R(4,4,4) R(3,3,3)", "R(4,4,4) S(7)",
-                 "R(4,4,4) G(7)", "R(3,3,3) G(8)", "S(7) G(4)", "S(5) G(6)", "S(3) G(8)", "S(11)", "G(11)",
-                 "R(2,2,2) R(1,1,1) S(4) G(4)"]
+# Table 2: the paper's label of each format (1-20 at 2048^3, 21-40 at 512^3).
+TABLE2_2048 = {1: "D(4,4,4,6) D(3,3,3,6) G(4)", 2: "D(4,4,4,6) R(3,3,3) G(4)", 3: "R(4,4,4) R(3,3,3) G(4)",
+               4: "R(4,4,4) S(3) G(4)", 5: "R(4,4,4) R(4,4,4) R(3,3,3)", 6: "D(4,4,4,6) S(7)",
+               7: "D(4,4,4,6) G(7)", 8: "D(6,6,6,6) S(5)", 9: "D(6,6,6,6) G(5)", 10: "R(4,4,4) S(7)",
+               11: "R(4,4,4) G(7)", 12: "R(6,6,6) S(5)", 13: "R(6,6,6) G(5)", 14: "R(3,3,3) G(8)",
+               15: "R(8,8,8) G(3)", 16: "S(7) G(4)", 17: "S(5) G(6)", 18: "S(3) G(8)", 19: "S(11)", 20: "G(11)"}
+TABLE2_512 = {21: "D(3,3,3,6) D(3,3,3,6) G(3)", 22: "D(3,3,3,6) R(3,3,3) G(3)", 23: "R(3,3,3) R(3,3,3) G(3)",
+              24: "R(3,3,3) R(3,3,3) R(3,3,3)", 25: "R(4,4,4) R(1,1,1) R(4,4,4)", 26: "D(4,4,4,6) S(5)",
+              27: "D(4,4,4,6) G(5)", 28: "R(4,4,4) S(5)", 29: "R(4,4,4) G(5)", 30: "R(2,2,2) G(7)",
+              31: "R(7,7,7) G(2)", 32: "S(5) R(4,4,4)", 33: "G(5) R(4,4,4)", 34: "D(5,5,5,6) D(4,4,4,6)",
+              35: "D(5,5,5,6) R(4,4,4)", 36: "R(5,5,5) R(4,4,4)", 37: "R(9,9,9)", 38: "D(9,9,9,6)", 39: "S(9)",
+              40: "G(9)"}
+# the 2048^3 sweep: all of Table 2's 2048^3 formats, plus one with 2^2 and 2^1 Raw levels
+SWEEP_FORMATS = list(TABLE2_2048.values()) + ["R(2,2,2) R(1,1,1) S(4) G(4)"]
+LABEL = {v: k for k, v in {**TABLE2_2048, **TABLE2_512}.items()}
 BATCH_FORMATS = ["R(3,3,3) G(8)", "R(4,4,4) G(7)", "R(4,4,4) S(3) G(4)", "R(4,4,4) R(3,3,3) G(4)"]
 SEED3 = 2048
 
@@ -514,7 +526,8 @@ def run_sweep(args):
             trav["restart" if rs else "stack"] = {"mrays_s_primary_plain": round(prim.shape[0] / mp / 1e3, 1),
                                                   "mrays_s_ao_persistent": round(ao.shape[0] / ma / 1e3, 1)}
         del prim, prim_hits
-        per.append({"format": spec, "build_s": round(build_s, 1), "device_bytes": st["device_bytes"],
+        per.append({"format": spec, "table2": LABEL.get(spec), "build_s": round(build_s, 1),
+                    "device_bytes": st["device_bytes"],
                     "bytes_per_voxel": round(st["device_bytes"] / 2048 ** 3, 6),
                     "bytes_per_occupied_voxel": round(st["device_bytes"] / max(1, st["occupied_voxels"]), 4),
                     "mrays_s_primary": round(len(cams) * n_prim / ms_prim / 1e3, 1),
@@ -534,6 +547,123 @@ def run_sweep(args):
                                              "(cosine-weighted, tmax 32) per format",
                                  "occupancy": round(sc.occupied / 2048 ** 3, 5)},
                       "per_format": per}), flush=True)
+    return 0
+
+
+def run_formats512(args):
+    """Every 512^3 format of Table 2 (plus the headline R(4,4,4) S(2) G(3)) on
+    the 512^3 terrain: size, build time, and Mrays/s of the 1080p view and of
+    the 2^21 incoherent rays (autotuned), so speed can be read against
+    bytes per voxel as in the paper's trade-off plots."""
+    import torch
+    import paper_2410_14128_b300 as vx
+    grid, cam, inc_np = make_inputs()
+    inc = torch.from_numpy(inc_np).cuda()
+    n_prim = WIDTH * HEIGHT
+    hp, hi = vx.alloc_hits(n_prim), vx.alloc_hits(N_INC)
+    per = []
+    for spec in list(TABLE2_512.values()) + ["R(4,4,4) S(2) G(3)"]:
+        t0 = time.perf_counter()
+        v = vx.Volume(spec, grid)
+        build_s = time.perf_counter() - t0
+        st = v.stats()
+        tune = v.autotune(inc[: 1 << 19]) if not args.no_tune else None
+        ms_r = _timed(torch, lambda: v.render(cam, hp), args.steps, args.warmup)
+        ms_t = _timed(torch, lambda: v.trace(inc, hi), args.steps, args.warmup)
+        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        v.trace_counted(inc, hi, c)
+        torch.cuda.synchronize()
+        b, it, _ = (int(x) for x in c.cpu())
+        per.append({"format": spec, "table2": LABEL.get(spec), "build_s": round(build_s, 2),
+                    "device_bytes": st["device_bytes"], "canonical_bytes": st["canonical_bytes"],
+                    "bytes_per_voxel": round(st["device_bytes"] / N_VOL ** 3, 5),
+                    "specialized_kernel": st["specialized"],
+                    "mrays_s_primary": round(n_prim / ms_r / 1e3, 1), "mrays_s_incoherent": round(N_INC / ms_t / 1e3, 1),
+                    "mrays_s": round((n_prim + N_INC) / (ms_r + ms_t) / 1e3, 1),
+                    "node_bytes_per_ray_incoherent": round(b / N_INC, 2), "iters_per_ray_incoherent": round(it / N_INC, 2),
+                    "tuned": tune})
+        v.free()
+        torch.cuda.empty_cache()
+    tot_ms = sum((n_prim + N_INC) / p["mrays_s"] / 1e3 for p in per)
+    print(json.dumps({"metric": METRIC, "workload": "formats512", "value": round(len(per) * (n_prim + N_INC) / tot_ms / 1e3, 2),
+                      "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "512^3 terrain; every Table 2 512^3 format; per format one 1920x1080 "
+                                             "view + 2^21 incoherent rays", "steps": args.steps},
+                      "per_format": per}), flush=True)
+    return 0
+
+
+def run_dedup(args):
+    """De-duplication scope (Sec. 4.3): every Table 2 format with an SVDAG
+    level, built with one map per sub-volume (the paper's default) and with
+    one map per level; sizes only (host build, no GPU)."""
+    import synth
+    import paper_2410_14128_b300 as vx
+    rows = []
+
+    def measure(spec, grid, palette, scene):
+        r = {"format": spec, "table2": LABEL.get(spec), "scene": scene}
+        for name, scope in (("per_subvolume", vx.DEDUP_PER_SUBVOLUME), ("whole_level", vx.DEDUP_WHOLE_LEVEL)):
+            t0 = time.perf_counter()
+            v = vx.Volume(spec, grid, palette=palette, dedup=scope, upload=False)
+            st = v.stats()
+            r[name] = {"bytes": st["canonical_bytes"], "build_s": round(time.perf_counter() - t0, 2),
+                       "level_bytes": [4 * w for w in st["level_words"]]}
+            v.free()
+        r["whole_over_per"] = round(r["whole_level"]["bytes"] / r["per_subvolume"]["bytes"], 4)
+        rows.append(r)
+
+    grid, _, _ = make_inputs()
+    for spec in TABLE2_512.values():
+        if "G(" in spec:
+            measure(spec, grid, None, "512^3 terrain")
+    del grid
+    sc, g8 = _scene2048()
+    for spec in TABLE2_2048.values():
+        if "G(" in spec:
+            measure(spec, g8, sc.palette, "2048^3 primitive scene")
+    print(json.dumps({"workload": "dedup", "metric": "canonical bytes per de-duplication scope",
+                      "data": "synthetic", "rows": rows}), flush=True)
+    return 0
+
+
+def _buildmem_one(spec: str):
+    """Child process: builds `spec` from the 2048^3 scene brick by brick
+    (the lazy voxelizer of Sec. 5) and prints its peak resident memory."""
+    import resource
+    import synth
+    import paper_2410_14128_b300 as vx
+    sc = synth.PrimitiveScene(SEED3, 2048)
+    base = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss
+    t0 = time.perf_counter()
+    v = vx.Volume(spec, log2_dim=(11, 11, 11), fill_brick=sc.fill_brick_fn, block_empty=sc.block_empty_fn,
+                  user=sc.handle, upload=False)
+    dt = time.perf_counter() - t0
+    st = v.stats()
+    peak = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss
+    print(json.dumps({"format": spec, "build_s": round(dt, 1), "canonical_bytes": st["canonical_bytes"],
+                      "peak_rss_bytes": peak * 1024, "rss_before_build_bytes": base * 1024}), flush=True)
+    return 0
+
+
+def run_buildmem(args):
+    """Out-of-core construction (Sec. 5): each 2048^3 format of the sweep is
+    built in its own process from 64^3 bricks produced on demand, and the
+    process's peak resident memory is recorded (the dense grid would take
+    32 GiB as RGBA words)."""
+    import subprocess
+    rows = []
+    for spec in SWEEP_FORMATS:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--buildmem-spec", spec],
+                             capture_output=True, text=True)
+        if out.returncode != 0:
+            rows.append({"format": spec, "error": out.stderr.strip().splitlines()[-1:]})
+            continue
+        r = json.loads(out.stdout.strip().splitlines()[-1])
+        r["table2"] = LABEL.get(spec)
+        rows.append(r)
+    print(json.dumps({"workload": "buildmem", "metric": "peak resident memory of a brick-by-brick build",
+                      "data": "synthetic", "dense_rgba_bytes": 4 * 2048 ** 3, "rows": rows}), flush=True)
     return 0
 
 
@@ -648,6 +778,18 @@ def run_serve(args):
                      "served": {"mrays_s": round(rays / span / 1e6, 1), **serve.latency_stats(rs), "epochs": srv.epochs},
                      "serial_plain": {"mrays_s": round(rays / span_s / 1e6, 1), **serve.latency_stats(ss)},
                      "results_identical": same})
+    # saturated: every request due at t = 0 (throughput of both paths)
+    reqs = requests(args.requests, 0, 7)
+    srv = serve.Server(vols, mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), keep_hits=False, digest_every=10)
+    res = srv.run(reqs, realtime=False)
+    ser = serve.serve_serial(vols, reqs, keep_hits=False, digest_every=10)
+    rays = sum(r.n for r in reqs)
+    rows.append({"rho": "saturated", "requests": len(reqs),
+                 "served": {"mrays_s": round(rays / max(r.done for r in res.values()) / 1e6, 1),
+                            **serve.latency_stats(res), "epochs": srv.epochs},
+                 "serial_plain": {"mrays_s": round(rays / max(r.done for r in ser.values()) / 1e6, 1),
+                                  **serve.latency_stats(ser)},
+                 "results_identical": all(res[i].digest == ser[i].digest for i in res if i % 10 == 0)})
     best = max(r["served"]["mrays_s"] for r in rows)
     print(json.dumps({"metric": METRIC, "workload": "serve", "value": best, "unit": UNIT, "n_gpus": 1,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -670,17 +812,27 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
-    ap.add_argument("--workload", default="terrain512", choices=["terrain512", "sweep2048", "batch", "serve"])
+    ap.add_argument("--workload", default="terrain512",
+                    choices=["terrain512", "formats512", "sweep2048", "batch", "serve", "dedup", "buildmem"])
+    ap.add_argument("--buildmem-spec", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sweep-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--warm-requests", type=int, default=200)
     ap.add_argument("--rhos", type=float, nargs="+", default=[0.5, 0.8, 0.95])
     args = ap.parse_args()
+    if args.buildmem_spec:
+        return _buildmem_one(args.buildmem_spec)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "dedup":
+        return run_dedup(args)
+    if args.workload == "buildmem":
+        return run_buildmem(args)
     if args.workload == "sweep2048":
         return run_sweep(args)
+    if args.workload == "formats512":
+        return run_formats512(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "serve":

@@ -60,8 +60,9 @@ __global__ void __launch_bounds__(256) k_trace_noalloc(DynF f, const Img pool,
                                                        int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint2 stack[DynF::kMaxJ];
     Walker<false, DynF> w;
-    bind_stack(w);
+    w.S = stack;
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint32_t idx = 0;
@@ -121,9 +122,8 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int block = 256;
-    const size_t sm = stack_bytes(V.spec.fmt.J, block);  // node stacks (shared memory, not allocated)
-    e = layout == VX_HIT_FULL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<0>, block, sm)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<1>, block, sm);
+    e = layout == VX_HIT_FULL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<0>, block, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<1>, block, 0);
     if (e) return fail(VX_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = (uint64_t)sms * per_sm;
@@ -135,10 +135,10 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     DynF f;
     f.p = V.spec.fmt;
     if (layout == VX_HIT_FULL)
-        k_trace_noalloc<0><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<0><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     else
-        k_trace_noalloc<1><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<1><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "vx_trace_noalloc launch: %s", cudaGetErrorString(e));

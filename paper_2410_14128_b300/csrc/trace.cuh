@@ -275,10 +275,8 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // without leaving the loop (persistent kernels).
 //
 // The node stack (pointer and valid mask of the node entered at each node
-// level) lives in shared memory, entry j of thread t at S[j * blockDim + t]:
-// lanes touch consecutive words whatever level each is at, so accesses are
-// free of bank conflicts, and the stack never competes with node reads for
-// L1 lines as a local-memory stack does.
+// level, one 8-byte entry per level) is an array of the calling kernel,
+// passed in as a pointer so that the walker's scalars stay in registers.
 //
 // RESTART selects the paper's restarting sparse-voxel intersection (Sec.
 // 4.4): only the root node of each format level is kept; leaving a node of
@@ -299,8 +297,7 @@ struct Walker {
     bool bot_c;
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
-    uint2* S;         // this thread's node stack: entry j at S[j * ss]
-    int ss;           // stack stride (threads of the block)
+    uint2* S;         // this thread's node stack, F::kMaxJ entries (owned by the caller)
     Cnt cnt;
 
     __device__ __forceinline__ void load_level(const F& f) {
@@ -318,7 +315,7 @@ struct Walker {
     __device__ __forceinline__ void restart(const F& f, const Img im) {
         const uint32_t* __restrict__ pool = im.w;
         const int r = 31 - __clz(f.top() & ((2u << j) - 1u));
-        const uint2 e = S[r * ss];
+        const uint2 e = S[r];
         uint32_t p = e.x, m = e.y;
         const bool svo = f.has_svo() && f.kind(r) == K_SVO;
         const int sj = f.s(j);
@@ -475,6 +472,84 @@ struct Walker {
         return false;
     }
 
+    // One Amanatides-Woo step at node level j, with the pop when the step
+    // leaves the node.  Returns true once the ray is finished (out holds the
+    // miss).
+    __device__ __forceinline__ bool advance(const F& f, const Img im, HitRec& out) {
+        if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) {
+            out = miss_rec(ST_MISS);
+            return true;
+        }
+        // next plane per axis and its crossing, in closed form from the cell
+        int pl[3];
+        float tn[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << s_c;
+            tn[i] = sg[i] != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
+        }
+        int a = tn[1] < tn[0] ? 1 : 0;
+        float tm = fminf(tn[0], tn[1]);
+        if (tn[2] < tm) { a = 2; tm = tn[2]; }
+        // second smallest crossing; a d = 0 axis (+inf) is never near
+        const float t2 = fminf(fmaxf(tn[0], tn[1]), fmaxf(fminf(tn[0], tn[1]), tn[2]));
+        const bool und = !(t2 - tm > gabs);
+        if (und) {
+            VX_CNT(fp64, 1);
+            a = argmin64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], pl[0], pl[1], pl[2]);
+            tm = sel3(tn, a);
+        }
+        // A step through the grid's boundary ends the walk whatever the exit
+        // comparison says; only an exit on another axis or at tmax can tie.
+        const int pla = sel3(pl, a), sga = sel3(sg, a);
+        bool out_now = pla == (sga > 0 ? (1 << f.ldim(a)) : 0);
+        if (!out_now) {
+            if (near(tm, tx)) {
+                VX_CNT(fp64, 1);
+                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
+                                  f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
+            } else {
+                out_now = !(tm < tx);
+            }
+        }
+        if (out_now) {
+            out = miss_rec(ST_MISS);
+            return true;
+        }
+        const int old = sel3(c, a);
+        const int nw = old + sga;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            if (i == a) c[i] = nw;
+        tcur = tm;
+        la = a;
+        lp = pla;
+        fresh = false;
+        const int h = 31 - __clz((uint32_t)(old ^ nw)) + s_c;  // highest changed voxel-coordinate bit
+        const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
+        if (h >= span) {
+            skip = 0;  // the distances are those of the node the walk left
+            if (h >= f.ldim(a)) {
+                out = miss_rec(ST_MISS);
+                return true;
+            }
+            const int jp = f.jpop(h);
+            const int sh = f.s(jp) - s_c;
+#pragma unroll
+            for (int i = 0; i < 3; i++) c[i] >>= sh;
+            j = jp;
+            if (RESTART) {
+                restart(f, im);
+            } else {
+                const uint2 e = S[j];
+                Pc = e.x;
+                Mc = e.y;
+            }
+            load_level(f);
+        }
+        return false;
+    }
+
     __device__ __forceinline__ bool step(const F& f, const Img im, HitRec& out) {
         const uint32_t* __restrict__ pool = im.w;
         if (--budget < 0) {
@@ -484,7 +559,6 @@ struct Walker {
         VX_CNT(iters, 1);
         const int J = f.J();
         const int kind = kind_c;
-        const int s = s_c;
         const int bx = b_c[0], by = b_c[1], bz = b_c[2];
         const uint32_t lx = (uint32_t)c[0] & ((1u << bx) - 1u);
         const uint32_t ly = (uint32_t)c[1] & ((1u << by) - 1u);
@@ -507,14 +581,14 @@ struct Walker {
                 --skip;
                 occ = false;
             } else {
+                // both words at once (same sector): a distance load issued
+                // after the cell word returns would add a second latency
                 const uint32_t a = Pc + 2u * idx;
                 w = ldw(pool, a);
-                VX_CNT(bytes, 4);
+                const uint32_t dist = ldw(pool, a + 1);
+                VX_CNT(bytes, 8);
                 occ = w != 0u;
-                if (!occ) {
-                    skip = (int)ldw(pool, a + 1) - 1;
-                    VX_CNT(bytes, 4);
-                }
+                if (!occ) skip = (int)dist - 1;
             }
         } else {
             occ = (Mc >> idx) & 1u;
@@ -558,7 +632,7 @@ struct Walker {
                 else { Pn = term; Mn = ldw(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
-            if (!RESTART || ((f.top() >> j) & 1u)) S[j * ss] = make_uint2(Pn, Mn);
+            if (!RESTART || ((f.top() >> j) & 1u)) S[j] = make_uint2(Pn, Mn);
             Pc = Pn;
             Mc = Mn;
             load_level(f);
@@ -588,100 +662,16 @@ struct Walker {
         }
 
         // ---- one Amanatides-Woo step at node level j ----
-        if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) {
-            out = miss_rec(ST_MISS);
-            return true;
-        }
-        // next plane per axis and its crossing, in closed form from the cell
-        int pl[3];
-        float tn[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << s;
-            tn[i] = sg[i] != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
-        }
-        int a = tn[1] < tn[0] ? 1 : 0;
-        float tm = fminf(tn[0], tn[1]);
-        if (tn[2] < tm) { a = 2; tm = tn[2]; }
-        // second smallest crossing; a d = 0 axis (+inf) is never near
-        const float t2 = fminf(fmaxf(tn[0], tn[1]), fmaxf(fminf(tn[0], tn[1]), tn[2]));
-        const bool und = !(t2 - tm > gabs);
-        if (und) {
-            VX_CNT(fp64, 1);
-            a = argmin64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], pl[0], pl[1], pl[2]);
-            tm = sel3(tn, a);
-        }
-        // A step through the grid's boundary ends the walk whatever the exit
-        // comparison says; only an exit on another axis or at tmax can tie.
-        const int pla = sel3(pl, a), sga = sel3(sg, a);
-        bool out_now = pla == (sga > 0 ? (1 << f.ldim(a)) : 0);
-        if (!out_now) {
-            if (near(tm, tx)) {
-                VX_CNT(fp64, 1);
-                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
-                                  f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
-            } else {
-                out_now = !(tm < tx);
-            }
-        }
-        if (out_now) {
-            out = miss_rec(ST_MISS);
-            return true;
-        }
-        const int old = sel3(c, a);
-        const int nw = old + sga;
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-            if (i == a) c[i] = nw;
-        tcur = tm;
-        la = a;
-        lp = pla;
-        fresh = false;
-        const int h = 31 - __clz((uint32_t)(old ^ nw)) + s;  // highest changed voxel-coordinate bit
-        const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
-        if (h >= span) {
-            skip = 0;  // the distances are those of the node the walk left
-            if (h >= f.ldim(a)) {
-                out = miss_rec(ST_MISS);
-                return true;
-            }
-            const int jp = f.jpop(h);
-            const int sh = f.s(jp) - s;
-#pragma unroll
-            for (int i = 0; i < 3; i++) c[i] >>= sh;
-            j = jp;
-            if (RESTART) {
-                restart(f, im);
-            } else {
-                const uint2 e = S[j * ss];
-                Pc = e.x;
-                Mc = e.y;
-            }
-            load_level(f);
-        }
-        return false;
+        return advance(f, im, out);
     }
 };
 #undef VX_CNT
 
-// Dynamic shared memory of every walker kernel: the node stacks of its
-// threads, stack_bytes(J, block) bytes.
-extern __shared__ uint2 vx_stack_smem[];
-
-__host__ __device__ __forceinline__ size_t stack_bytes(uint32_t J, int block) {
-    return (size_t)J * (size_t)block * sizeof(uint2);
-}
-
-template <class Wk>
-__device__ __forceinline__ void bind_stack(Wk& w) {
-    w.S = vx_stack_smem + threadIdx.x;
-    w.ss = (int)blockDim.x;
-}
-
 template <bool COUNT, class F, bool RESTART = false>
 __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt) {
+    uint2 stack[F::kMaxJ];
     Walker<COUNT, F, RESTART> w;
-    bind_stack(w);
+    w.S = stack;
     HitRec h;
     if (!w.start(f, pool, r, h))
         while (!w.step(f, pool, h)) {
@@ -802,8 +792,9 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
                                                            unsigned long long* next, int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint2 stack[F::kMaxJ];
     Walker<false, F> w;
-    bind_stack(w);
+    w.S = stack;
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t slot = 0;
@@ -857,8 +848,9 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
                                                           int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint2 stack[F::kMaxJ];
     Walker<false, F, RS> w;
-    bind_stack(w);
+    w.S = stack;
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -916,8 +908,9 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t n = desc.start[desc.count];
+    uint2 stack[F::kMaxJ];
     Walker<false, F> w;
-    bind_stack(w);
+    w.S = stack;
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -1013,11 +1006,10 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        const size_t sm = stack_bytes(p.J, block);
-        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else k_trace<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        else k_trace<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
         return (int)cudaGetLastError();
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
@@ -1025,15 +1017,14 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        const size_t sm = stack_bytes(p.J, block);
         if (layout == 0 && !restart)
-            k_trace_count<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         else if (layout == 0)
-            k_trace_count<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         else if (!restart)
-            k_trace_count<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         else
-            k_trace_count<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
@@ -1045,14 +1036,13 @@ struct Launch {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t sm = stack_bytes(p.J, block);
         int per_sm = blocks_per_sm;
         if (per_sm <= 0) {
             cudaError_t e;
-            if (layout == 0 && !restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, false>, block, sm);
-            else if (layout == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, true>, block, sm);
-            else if (!restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, false>, block, sm);
-            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, true>, block, sm);
+            if (layout == 0 && !restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, false>, block, 0);
+            else if (layout == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, true>, block, 0);
+            else if (!restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, false>, block, 0);
+            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, true>, block, 0);
             if (e) return (int)e;
             if (per_sm < 1) per_sm = 1;
         }
@@ -1063,31 +1053,29 @@ struct Launch {
         if (e) return (int)e;
         const unsigned g = (unsigned)grid;
         if (layout == 0 && !restart)
-            k_trace_persistent<F, 0, false><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+            k_trace_persistent<F, 0, false><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         else if (layout == 0)
-            k_trace_persistent<F, 0, true><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+            k_trace_persistent<F, 0, true><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         else if (!restart)
-            k_trace_persistent<F, 1, false><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+            k_trace_persistent<F, 1, false><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         else
-            k_trace_persistent<F, 1, true><<<g, block, sm, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+            k_trace_persistent<F, 1, true><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
-        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, sm)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, sm);
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, 0);
         if (*per_sm < 1) *per_sm = 1;
         return (int)e;
     }
     static int trace_batch(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill,
                            int burst, cudaStream_t st, unsigned long long* next) {
         const F f = make(p);
-        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
-        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
-        else k_trace_batch<F, 1><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
+        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
+        else k_trace_batch<F, 1><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render_persistent(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -1098,10 +1086,9 @@ struct Launch {
         int dev = 0, sms = 0, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, sm)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, sm);
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, 0);
         if (e) return (int)e;
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)sms * per_sm;
@@ -1110,9 +1097,9 @@ struct Launch {
         e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         if (layout == 0)
-            k_render_persistent<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         else
-            k_render_persistent<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -1120,9 +1107,8 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        const size_t sm = stack_bytes(p.J, block);
-        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits);
-        else k_render<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits);
+        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
+        else k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
         return (int)cudaGetLastError();
     }
 };

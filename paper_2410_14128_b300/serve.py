@@ -197,7 +197,8 @@ class Server:
 def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.perf_counter,
                  keep_hits: bool = True, digest_every: int = 1) -> dict:
     """The plain path: one request at a time, in arrival order, each traced by
-    its own launch (render, or copy + plain trace) and waited for."""
+    its own launch (render, or copy + plain trace), its hits copied to pinned
+    host memory, and waited for."""
     import torch
     from . import MODE_PLAIN
     reqs = sorted(requests, key=lambda r: r.arrival)
@@ -217,7 +218,10 @@ def serve_serial(volumes: dict, requests, layout: int = HIT_FULL, clock=time.per
         else:
             rays = torch.from_numpy(req.rays).cuda()
             vol.trace(rays, hits, layout, mode=MODE_PLAIN)
-        h = hits.cpu().numpy().view(hit_dtype(layout)).reshape(-1)
+        host = torch.empty(hits.shape, dtype=hits.dtype, pin_memory=True)
+        host.copy_(hits, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        h = host.numpy().view(hit_dtype(layout)).reshape(-1)
         done = clock() - t0
         dg = digest(h) if req.id % max(1, digest_every) == 0 else None
         results[req.id] = Result(req.id, h if keep_hits else None, req.arrival, start, done, digest=dg)
