@@ -760,11 +760,12 @@ def run_serve(args):
     serve.serve_serial(vols, cal)
     cap = len(cal) / (time.perf_counter() - t0)
     rows = []
+    budget = int(args.serve_budget_gb * (1 << 30))
+    arena = serve.HostArena(budget)  # pinned download space, shared by the servers below
     for rho in args.rhos:
         rate = rho * cap
         reqs = requests(args.requests + args.warm_requests, rate, int(rho * 1000))
-        srv = serve.Server(vols, mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), keep_hits=False,
-                           digest_every=10)
+        srv = serve.Server(vols, mem_budget_bytes=budget, keep_hits=False, digest_every=10, host_arena=arena)
         res = srv.run(reqs, realtime=True)
         ser = serve.serve_serial(vols, reqs, keep_hits=False, digest_every=10)
         keep = [r.id for r in reqs[args.warm_requests:]]
@@ -780,7 +781,7 @@ def run_serve(args):
                      "results_identical": same})
     # saturated: every request due at t = 0 (throughput of both paths)
     reqs = requests(args.requests, 0, 7)
-    srv = serve.Server(vols, mem_budget_bytes=int(args.serve_budget_gb * (1 << 30)), keep_hits=False, digest_every=10)
+    srv = serve.Server(vols, mem_budget_bytes=budget, keep_hits=False, digest_every=10, host_arena=arena)
     res = srv.run(reqs, realtime=False)
     ser = serve.serve_serial(vols, reqs, keep_hits=False, digest_every=10)
     rays = sum(r.n for r in reqs)

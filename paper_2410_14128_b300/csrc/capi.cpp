@@ -85,7 +85,7 @@ size_t hit_bytes(int layout) { return layout == VX_HIT_FULL ? sizeof(vx_hit) : s
 int ensure_staging(Volume& V) {
     Staging& S = V.staging;
     if (S.ready) return VX_OK;
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < Staging::kDepth; i++) {
         cudaError_t e = cudaMalloc(&S.d_rays[i], Staging::kChunk * sizeof(vx_ray));
         if (e) return cuda_fail(e, "cudaMalloc (staging rays)");
         e = cudaMalloc(&S.d_hits[i], Staging::kChunk * sizeof(vx_hit));
@@ -103,7 +103,7 @@ int ensure_staging(Volume& V) {
 }
 
 void free_staging(Staging& S) {
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < Staging::kDepth; i++) {
         if (S.d_rays[i]) cudaFree(S.d_rays[i]);
         if (S.d_hits[i]) cudaFree(S.d_hits[i]);
         if (S.streams[i]) cudaStreamDestroy((cudaStream_t)S.streams[i]);
@@ -113,8 +113,9 @@ void free_staging(Staging& S) {
     S.ready = nullptr;
 }
 
-// Runs `work(k, i0, n, d_rays, d_hits, stream)` over chunks of the input on
-// two streams, so the copies of one chunk overlap the kernel of the other.
+// Runs `work(i0, n, d_rays, d_hits, stream)` over chunks of the input on
+// Staging::kDepth streams in turn, so copies in both directions overlap the
+// kernels of other chunks.
 template <class Work>
 int pipeline(Volume& V, uint64_t n, void* stream, Work work) {
     std::lock_guard<std::mutex> lock(V.staging_mu);
@@ -124,18 +125,18 @@ int pipeline(Volume& V, uint64_t n, void* stream, Work work) {
     cudaEvent_t ready = (cudaEvent_t)S.ready;
     cudaError_t e = cudaEventRecord(ready, (cudaStream_t)stream);
     if (e) return cuda_fail(e, "cudaEventRecord");
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < Staging::kDepth; i++) {
         e = cudaStreamWaitEvent((cudaStream_t)S.streams[i], ready, 0);
         if (e) return cuda_fail(e, "cudaStreamWaitEvent");
     }
     uint64_t k = 0;
     for (uint64_t i0 = 0; i0 < n; i0 += Staging::kChunk, k++) {
         const uint64_t m = (n - i0) < Staging::kChunk ? (n - i0) : Staging::kChunk;
-        const int b = (int)(k & 1);
+        const int b = (int)(k % Staging::kDepth);
         rc = work(i0, m, S.d_rays[b], S.d_hits[b], (cudaStream_t)S.streams[b]);
         if (rc) break;
     }
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < Staging::kDepth; i++) {
         e = cudaStreamSynchronize((cudaStream_t)S.streams[i]);
         if (e && !rc) rc = cuda_fail(e, "trace pipeline");
     }

@@ -566,33 +566,24 @@ struct Walker {
         // child index: x + (y << W) + (z << (W+H)) for Raw; the same formula
         // gives x | y << 1 | z << 2 inside an octree node (W = H = D = 1)
         const uint32_t idx = lx | (ly << bx) | (lz << (bx + by));
-        uint32_t w = 0;
-        bool occ;
-        if (kind == K_RAW) {
-            w = ldw(pool, Pc + idx);
-            VX_CNT(bytes, 4);
-            occ = w != 0u;
-        } else if (f.has_df() && kind == K_DF) {
-            // DF cell {terminating integer, L1 distance d}: every cell within
-            // L1 distance d - 1 is empty, and each Amanatides-Woo step moves
-            // one cell along one axis, so the next d - 1 cells of the walk at
-            // this level are entered without reading them (Sec. 4.2).
-            if (skip > 0) {
-                --skip;
-                occ = false;
-            } else {
-                // both words at once (same sector): a distance load issued
-                // after the cell word returns would add a second latency
-                const uint32_t a = Pc + 2u * idx;
-                w = ldw(pool, a);
-                const uint32_t dist = ldw(pool, a + 1);
-                VX_CNT(bytes, 8);
-                occ = w != 0u;
-                if (!occ) skip = (int)dist - 1;
-            }
-        } else {
-            occ = (Mc >> idx) & 1u;
-        }
+        // The look-up is written without divergent branches (loads under a
+        // predicate, results by selects): lanes at different kinds of level,
+        // or DF lanes that skip and lanes that read, stay together and reach
+        // the step below as one group.
+        const bool is_raw = kind == K_RAW;
+        const bool is_df = f.has_df() && kind == K_DF;
+        // DF cell {terminating integer, L1 distance d}: every cell within L1
+        // distance d - 1 is empty, and each Amanatides-Woo step moves one cell
+        // along one axis, so the next d - 1 cells of the walk at this level
+        // are entered without reading them (Sec. 4.2).
+        const bool df_read = is_df && skip <= 0;
+        const uint32_t a = is_df ? Pc + 2u * idx : Pc + idx;
+        uint32_t w = 0, dist = 0;
+        if (is_raw || df_read) w = ldw(pool, a);
+        if (df_read) dist = ldw(pool, a + 1);  // same sector, issued with the cell word
+        VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
+        const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;
+        if (is_df) skip = df_read ? (occ ? 0 : (int)dist - 1) : skip - 1;
         if (occ) {
             // ---- descend (or hit at the last node level) ----
             uint32_t term = w, Pn = 0, Mn = 0;

@@ -99,11 +99,15 @@ struct CameraParams {
 struct KernelSet;  // kernels for one format (trace.cuh)
 
 // Device buffers and streams of the *_host calls (chunked copy/trace pipeline).
+// kDepth chunks in flight on kDepth streams: the upload of one chunk, the
+// kernel of another and the download of a third overlap (PCIe moves data both
+// ways at once).
 struct Staging {
-    static constexpr uint64_t kChunk = 1u << 20;  // rays per chunk
-    void* d_rays[2] = {nullptr, nullptr};
-    void* d_hits[2] = {nullptr, nullptr};
-    void* streams[2] = {nullptr, nullptr};
+    static constexpr uint64_t kChunk = 1u << 18;  // rays per chunk
+    static constexpr int kDepth = 4;
+    void* d_rays[kDepth] = {};
+    void* d_hits[kDepth] = {};
+    void* streams[kDepth] = {};
     void* ready = nullptr;
 };
 

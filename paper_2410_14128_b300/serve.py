@@ -7,11 +7,13 @@ clock).  Each loop iteration
 1. admits arrived requests in arrival order while their device buffers
    (rays + hits) fit in the free part of the memory budget and an in-flight
    slot is free -- a request larger than the whole budget is refused;
-2. launches every admitted request as one *epoch* on the next of several
-   CUDA streams: trace requests copy their rays in and are traced together by
-   one ``vx_trace_batch`` call (grouped by format inside the library), render
-   requests run ``vx_render``; each request's hits are copied back to pinned
-   host memory and an event marks completion;
+2. launches every admitted request as one *epoch*: each render request runs
+   ``vx_render`` on the next of a pool of CUDA streams and copies its hits
+   back to pinned host memory on that stream, so one request's download
+   overlaps other requests' kernels; the epoch's trace requests copy their
+   rays in and are traced together by one ``vx_trace_batch`` call (grouped by
+   format inside the library) on the next stream, then copied back; an event
+   per request marks completion;
 3. polls the events of earlier epochs and completes finished requests,
    releasing their budget.
 
@@ -54,6 +56,48 @@ def digest(hits: np.ndarray) -> tuple:
     return (int(np.bitwise_xor.reduce(a)), int(a.sum(dtype=np.uint64)), a.size)
 
 
+class HostArena:
+    """One pinned host buffer, carved into the downloads of requests in
+    flight (first fit over a sorted free list, neighbours merged on free).
+    Pinning memory is slow -- milliseconds per buffer -- so the server pins
+    its whole download space once instead of once per request."""
+
+    ALIGN = 256
+
+    def __init__(self, nbytes: int):
+        import torch
+        self.nbytes = int(nbytes)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, pin_memory=True)
+        self.free = [(0, self.nbytes)]  # sorted (offset, size) extents
+
+    def alloc(self, n: int):
+        n = (int(n) + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        for k, (off, size) in enumerate(self.free):
+            if size >= n:
+                if size == n:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (off + n, size - n)
+                return off, n
+        return None
+
+    def release(self, off: int, n: int):
+        fl = self.free
+        k = 0
+        while k < len(fl) and fl[k][0] < off:
+            k += 1
+        fl.insert(k, (off, n))
+        if k + 1 < len(fl) and fl[k][0] + fl[k][1] == fl[k + 1][0]:
+            fl[k] = (fl[k][0], fl[k][1] + fl[k + 1][1])
+            fl.pop(k + 1)
+        if k > 0 and fl[k - 1][0] + fl[k - 1][1] == fl[k][0]:
+            fl[k - 1] = (fl[k - 1][0], fl[k - 1][1] + fl[k][1])
+            fl.pop(k)
+
+    def view(self, off: int, nbytes: int):
+        return self.buf[off:off + nbytes]
+
+
 @dataclasses.dataclass
 class Result:
     id: int
@@ -70,8 +114,9 @@ class Result:
 
 
 class Server:
-    def __init__(self, volumes: dict, mem_budget_bytes: int, max_inflight: int = 256, streams: int = 3,
-                 layout: int = HIT_FULL, clock=time.perf_counter, keep_hits: bool = True, digest_every: int = 1):
+    def __init__(self, volumes: dict, mem_budget_bytes: int, max_inflight: int = 256, streams: int = 4,
+                 layout: int = HIT_FULL, clock=time.perf_counter, keep_hits: bool = True, digest_every: int = 1,
+                 host_arena: HostArena | None = None):
         import torch
         self.torch = torch
         self.volumes = volumes
@@ -84,7 +129,11 @@ class Server:
         self.clock = clock
         self.t0 = clock()
         self.pending: deque = deque()
-        self.inflight: list = []  # (req, admitted_time, bytes, event, host_hits, keep)
+        # per stream, in launch order: (req, admitted_time, bytes, event, host_buffer, keep)
+        self.inflight = [deque() for _ in self.streams]
+        self.n_inflight = 0
+        # pinned download space, as large as the device budget by default
+        self.arena = host_arena or HostArena(self.budget)
         self.results: dict = {}
         self.epochs = 0
         self.keep_hits = keep_hits  # else keep only a digest of each result
@@ -106,7 +155,7 @@ class Server:
         torch = self.torch
         now = self.now()
         admitted = []
-        while self.pending and self.pending[0].arrival <= now and len(self.inflight) + len(admitted) < self.max_inflight:
+        while self.pending and self.pending[0].arrival <= now and self.n_inflight + len(admitted) < self.max_inflight:
             req = self.pending[0]
             need = self.bytes_for(req)
             if need > self.budget:
@@ -115,56 +164,83 @@ class Server:
                 continue
             if self.used + need > self.budget:
                 break  # wait for memory (arrival order is kept)
+            slot = self.arena.alloc(HIT_BYTES[self.layout] * req.n)
+            if slot is None:
+                if self.n_inflight + len(admitted) == 0:  # cannot fit even alone
+                    self.pending.popleft()
+                    self.results[req.id] = Result(req.id, None, req.arrival, now, now,
+                                                  refused="larger than the host download space")
+                    continue
+                break  # wait for host download space
             self.pending.popleft()
             self.used += need
-            admitted.append((req, need))
+            admitted.append((req, need, slot))
         if admitted:
             self._launch(admitted, now)
         return self._poll()
 
+    def _stream(self):
+        k = self.next_stream
+        self.next_stream = (self.next_stream + 1) % len(self.streams)
+        return k, self.streams[k]
+
+    def _finish(self, req, now, need, slot, hits, keep, k, stream):
+        # download on the request's stream into its slot of the pinned arena;
+        # the event marks completion
+        torch = self.torch
+        nbytes = hits.numel() * hits.element_size()
+        buf = self.arena.view(slot[0], nbytes)
+        buf.view(hits.dtype).view(hits.shape).copy_(hits, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        self.inflight[k].append((req, now, need, ev, (slot, buf), keep))
+        self.n_inflight += 1
+
     def _launch(self, admitted, now):
         torch = self.torch
-        stream = self.streams[self.next_stream]
-        self.next_stream = (self.next_stream + 1) % len(self.streams)
         self.epochs += 1
-        batch = []
-        launched = []
-        with torch.cuda.stream(stream):
-            for req, need in admitted:
-                vol = self.volumes[req.volume]
+        traces = []
+        for req, need, slot in admitted:
+            vol = self.volumes[req.volume]
+            if req.camera is None:
+                traces.append((req, need, slot, vol))
+                continue
+            k, stream = self._stream()
+            with torch.cuda.stream(stream):
                 hits = alloc_hits(req.n, self.layout)
-                keep = [hits]
-                if req.camera is not None:
-                    vol.render(req.camera, hits, self.layout, stream=stream)
-                else:
+                vol.render(req.camera, hits, self.layout, stream=stream)
+                self._finish(req, now, need, slot, hits, [hits], k, stream)
+        if traces:
+            k, stream = self._stream()
+            with torch.cuda.stream(stream):
+                batch, launched = [], []
+                for req, need, slot, vol in traces:
+                    hits = alloc_hits(req.n, self.layout)
                     rays = torch.from_numpy(req.rays).to("cuda", non_blocking=True)
-                    keep.append(rays)
                     batch.append((vol, rays, hits))
-                launched.append((req, need, hits, keep))
-            if batch:
+                    launched.append((req, need, slot, hits, [hits, rays]))
                 trace_batch(batch, self.layout, stream=stream)
-            for req, need, hits, keep in launched:
-                host = torch.empty(hits.shape, dtype=hits.dtype, pin_memory=True)
-                host.copy_(hits, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(stream)
-                self.inflight.append((req, now, need, ev, host, keep))
+                for req, need, slot, hits, keep in launched:
+                    self._finish(req, now, need, slot, hits, keep, k, stream)
 
     def _poll(self) -> int:
+        # work on one stream completes in launch order: look at each stream's
+        # oldest request only
         done = 0
-        still = []
-        for item in self.inflight:
-            req, adm, need, ev, host, keep = item
-            if ev.query():
+        for q in self.inflight:
+            while q and q[0][3].query():
+                req, adm, need, ev, (slot, buf), keep = q.popleft()
                 t = self.now()
-                h = host.numpy().view(hit_dtype(self.layout)).reshape(-1)
+                h = buf.numpy().view(hit_dtype(self.layout)).reshape(-1)
                 dg = digest(h) if req.id % self.digest_every == 0 else None
-                self.results[req.id] = Result(req.id, h if self.keep_hits else None, req.arrival, adm, t, digest=dg)
+                if self.keep_hits:
+                    self.results[req.id] = Result(req.id, h.copy(), req.arrival, adm, t, digest=dg)
+                else:
+                    self.results[req.id] = Result(req.id, None, req.arrival, adm, t, digest=dg)
+                self.arena.release(*slot)
                 self.used -= need
+                self.n_inflight -= 1
                 done += 1
-            else:
-                still.append(item)
-        self.inflight = still
         return done
 
     # -- driver ---------------------------------------------------------------
@@ -186,7 +262,7 @@ class Server:
             self.step()
             if now > timeout_s:
                 raise TimeoutError(f"serving did not finish in {timeout_s} s")
-            if not self.inflight and not self.pending and i < total:
+            if self.n_inflight == 0 and not self.pending and i < total:
                 # idle until the next arrival
                 wait = reqs[i].arrival - self.now()
                 if wait > 0:
