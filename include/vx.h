@@ -204,7 +204,10 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *   block  threads per block: 0 = default, else a multiple of 32 in
  *          [32, 256] (VX_EINVAL otherwise);
  *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = as many as fit;
- *   smem_top  reserved (0);
+ *   smem_top  persistent mode: 1 = each block first copies the top level
+ *          into shared memory and reads its cells there (a Raw or DF top
+ *          level of at most 8192 words, without restart; ignored otherwise);
+ *          0 = off.  Any other value: VX_EINVAL;
  *   refill persistent mode: a warp fetches new rays once this many of its
  *          lanes are idle (1..32), 0 = default;
  *   burst  persistent mode: loop iterations between refill checks, 0 = default;

@@ -138,9 +138,10 @@ def _check(rc: int):
         raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
 
 
-def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False):
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False, smem_top=False):
     o = _TraceOpts()
-    o.mode, o.block, o.blocks_per_sm, o.smem_top, o.refill, o.burst = mode, block, blocks_per_sm, 0, refill, burst
+    o.mode, o.block, o.blocks_per_sm, o.refill, o.burst = mode, block, blocks_per_sm, refill, burst
+    o.smem_top = int(smem_top)
     o.sort_cell_log2 = sort
     o.restart = int(restart)
     return o
@@ -312,6 +313,7 @@ class Volume:
                                  _stream_handle(stream), ctypes.byref(o), ctypes.byref(ms)))
         return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
                 "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
+                "smem_top": bool(o.smem_top),
                 "sample_ms": ms.value}
 
     def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,

@@ -70,6 +70,7 @@ int check_opts(const vx_trace_opts* o) {
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
         return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
     if (o->restart != 0 && o->restart != 1) return fail(VX_EINVAL, "restart must be 0 or 1, got %d", o->restart);
+    if (o->smem_top != 0 && o->smem_top != 1) return fail(VX_EINVAL, "smem_top must be 0 or 1, got %d", o->smem_top);
     return VX_OK;
 }
 
@@ -386,6 +387,16 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
     bool deep_octree = false;
     for (const Level& L : V.spec.lv) deep_octree |= (L.kind == K_SVO || L.kind == K_DAG) && L.e[0] >= 2;
     if (deep_octree) { vx_trace_opts c = cur; c.restart = 1; consider(c); }
+    // staging applies to a Raw / DF top level of at most 8192 words
+    {
+        const Level& L0 = V.spec.lv[0];
+        const uint64_t words = (1ull << (L0.e[0] + L0.e[1] + L0.e[2])) * (L0.kind == K_DF ? 2u : 1u);
+        if ((L0.kind == K_RAW || L0.kind == K_DF) && words <= 8192 && !cur.restart) {
+            vx_trace_opts c = cur;
+            c.smem_top = 1;
+            consider(c);
+        }
+    }
     const int maxg = std::min(V.spec.ldim[0], std::min(V.spec.ldim[1], V.spec.ldim[2]));
     for (int g : {2, 3, 4, 5, 6, 7}) {
         if (g > maxg) break;

@@ -168,8 +168,9 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
+        const int smem_top = o ? o->smem_top : 0;
         e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits,
-                                        layout, block, bps, refill, burst, restart, st, next);
+                                        layout, block, bps, refill, burst, restart, smem_top, st, next);
     } else {
         e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
                              block, restart, st);

@@ -283,7 +283,13 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // 4.4): only the root node of each format level is kept; leaving a node of
 // an SVO or SVDAG level walks that level's octree again from its root down
 // to the resuming node level, at the price of re-reading those nodes.
-template <bool COUNT, class F, bool RESTART = false>
+//
+// TOPS: the cells of node level 0 (a Raw or DF top level) were copied into
+// vx_top_smem by the calling kernel, and level-0 look-ups read them there.
+extern __shared__ uint32_t vx_top_smem[];
+constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB: R(4,4,4) or D(4,4,4,M)
+
+template <bool COUNT, class F, bool RESTART = false, bool TOPS = false>
 struct Walker {
     RayIn r;
     float inv[3];
@@ -579,9 +585,11 @@ struct Walker {
         // are entered without reading them (Sec. 4.2).
         const bool df_read = is_df && skip <= 0;
         const uint32_t a = is_df ? Pc + 2u * idx : Pc + idx;
+        const uint32_t as = is_df ? 2u * idx : idx;  // word of the cell in a staged top level
+        const bool staged = TOPS && j == 0;
         uint32_t w = 0, dist = 0;
-        if (is_raw || df_read) w = ldw(pool, a);
-        if (df_read) dist = ldw(pool, a + 1);  // same sector, issued with the cell word
+        if (is_raw || df_read) w = staged ? vx_top_smem[as] : ldw(pool, a);
+        if (df_read) dist = staged ? vx_top_smem[as + 1] : ldw(pool, a + 1);  // same sector as the cell word
         VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
         const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;
         if (is_df) skip = df_read ? (occ ? 0 : (int)dist - 1) : skip - 1;
@@ -832,16 +840,26 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // the idle lanes in lane order (ballot + popc rank + shuffle); busy lanes keep
 // walking.  Each round advances every live lane by up to `burst` iterations.
 // `next` must be zero at launch; the kernel leaves it >= n.
-template <class F, int LAYOUT, bool RS = false>
+//
+// TS: the block first copies the top level's `top_words` words (a Raw or DF
+// level 0, at most kTopSmemMaxWords) into shared memory; the launch provides
+// 4 top_words bytes of dynamic shared memory.
+template <class F, int LAYOUT, bool RS = false, bool TS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
                                                           const uint32_t* __restrict__ order, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
-                                                          int refill, int burst) {
+                                                          int refill, int burst, uint32_t top_words) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
+    if (TS) {
+        const uint32_t root = ldw(pool.w, 0);
+        if (root != 0)
+            for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) vx_top_smem[i] = ldw(pool.w, root + i);
+        __syncthreads();
+    }
     uint2 stack[F::kMaxJ];
-    Walker<false, F, RS> w;
+    Walker<false, F, RS, TS> w;
     w.S = stack;
     bool live = false;
     bool exhausted = false;  // warp-uniform
@@ -980,7 +998,7 @@ struct KernelSet {
                        int layout, int block, int restart, cudaStream_t st, unsigned long long* counters);
     int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
-                            int restart, cudaStream_t st, unsigned long long* next);
+                            int restart, int smem_top, cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
     int (*trace_batch)(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill, int burst,
                        cudaStream_t st, unsigned long long* next);
@@ -1019,22 +1037,27 @@ struct Launch {
             k_trace_count<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
         return (int)cudaGetLastError();
     }
-    // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
-    static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
-                                uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
-                                int burst, int restart, cudaStream_t st, unsigned long long* next) {
-        if (n == 0) return 0;
-        const F f = make(p);
+    // Words of a Raw / DF top level that fits the shared-memory staging, else 0.
+    static uint32_t top_words(const FmtParams& p) {
+        const int k0 = fp_kind(p, 0);
+        if (k0 != K_RAW && k0 != K_DF) return 0;
+        const uint64_t cells = 1ull << (p.b0[0] + p.b0[1] + p.b0[2]);
+        const uint64_t words = cells * (k0 == K_DF ? 2u : 1u);
+        return words <= kTopSmemMaxWords ? (uint32_t)words : 0u;
+    }
+    template <bool RS, bool TS>
+    static int persistent_as(const F& f, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+                             void* hits, int layout, int block, int per_sm_req, int refill, int burst,
+                             cudaStream_t st, unsigned long long* next, uint32_t tw) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int per_sm = blocks_per_sm;
+        const size_t smem = TS ? (size_t)tw * sizeof(uint32_t) : 0;
+        int per_sm = per_sm_req;
         if (per_sm <= 0) {
-            cudaError_t e;
-            if (layout == 0 && !restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, false>, block, 0);
-            else if (layout == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, true>, block, 0);
-            else if (!restart) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, false>, block, 0);
-            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, true>, block, 0);
+            cudaError_t e = layout == 0
+                                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, RS, TS>, block, smem)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, RS, TS>, block, smem);
             if (e) return (int)e;
             if (per_sm < 1) per_sm = 1;
         }
@@ -1044,15 +1067,29 @@ struct Launch {
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         const unsigned g = (unsigned)grid;
-        if (layout == 0 && !restart)
-            k_trace_persistent<F, 0, false><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
-        else if (layout == 0)
-            k_trace_persistent<F, 0, true><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
-        else if (!restart)
-            k_trace_persistent<F, 1, false><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+        if (layout == 0)
+            k_trace_persistent<F, 0, RS, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw);
         else
-            k_trace_persistent<F, 1, true><<<g, block, 0, st>>>(f, pool, rays, order, n, hits, next, refill, burst);
+            k_trace_persistent<F, 1, RS, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw);
         return (int)cudaGetLastError();
+    }
+    // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
+    // smem_top: stage a Raw / DF top level of at most kTopSmemMaxWords words in
+    // shared memory (ignored for other formats; not combined with restart).
+    static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
+                                uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
+                                int burst, int restart, int smem_top, cudaStream_t st, unsigned long long* next) {
+        if (n == 0) return 0;
+        const F f = make(p);
+        const uint32_t tw = top_words(p);
+        if (restart)
+            return persistent_as<true, false>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                              burst, st, next, 0);
+        if (smem_top && tw)
+            return persistent_as<false, true>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                              burst, st, next, tw);
+        return persistent_as<false, false>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                           burst, st, next, 0);
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
         cudaError_t e = layout == 0

@@ -514,3 +514,23 @@ def test_df_packed_restart_persistent(spec):
                     ref = got
                     compare(g, rays, ref)
                 assert np.array_equal(got, ref), (canonical, mode, restart)
+
+
+# ---------------------------------------------------------------------------
+# Top level staged in shared memory (persistent kernel): same hits
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "R(4,4,4) G(3)", "D(4,4,4,6) G(3)", "R(2,2,2) R(2,2,2) R(3,3,3)",
+                                  "S(1) G(2) R(2,2,2) S(2)", "R(5,5,5) R(2,2,2)"])
+def test_smem_top_equals_plain(spec):
+    g = synth.terrain_volume(121, 128)
+    rays = np.concatenate([synth.incoherent_rays(122, 128, 60001), synth.box_rays(123, 128, 40, 20000),
+                           lattice_rays(124, (128, 128, 128), 5000)])
+    vol = vx.Volume(spec, g)
+    ref = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    compare(g, rays, ref)
+    for block, refill, burst in [(256, 8, 4), (64, 1, 1), (128, 32, 16)]:
+        for rep in range(2):
+            got = gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, smem_top=True, block=block, refill=refill, burst=burst)
+            assert np.array_equal(got, ref), (block, refill, burst, rep)
+    with pytest.raises(vx.VxError):
+        gpu_trace(vol, rays, smem_top=2)
