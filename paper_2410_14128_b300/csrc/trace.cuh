@@ -39,12 +39,18 @@ namespace vx {
 
 constexpr float kGuard = 9.5367431640625e-07f;  // 2^-20
 
-// Resident blocks per SM the persistent kernels are compiled for.  Measured
-// on the 512^3 terrain step: 4 (64 registers a thread, some spills) beats 3
-// (80 registers) by 1.7%, and 3 beats 2.
+// Resident blocks of 256 threads per SM the kernels are compiled for
+// (64 registers a thread, some spills).  Measured on the 512^3 terrain step:
+// persistent kernels at 4 beat 3 (80 registers) by 1.7%, and 3 beats 2;
+// the one-ray-per-thread kernels at 4 beat the unconstrained build (80
+// registers) by 7-11% on primary rays.
 #ifndef VX_PERSIST_MINB
 #define VX_PERSIST_MINB 4
 #endif
+#ifndef VX_PLAIN_MINB
+#define VX_PLAIN_MINB 4
+#endif
+#define VX_PLAIN_BOUNDS __launch_bounds__(256, VX_PLAIN_MINB)
 
 enum : uint32_t { ST_MISS = 0, ST_HIT = 1, ST_INVALID = 2, ST_ERROR = 3 };
 
@@ -745,7 +751,7 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // `order` (optional): launch slot k traces ray order[k] and writes its hit
 // at order[k] (rays sorted for coherence, results in the caller's order).
 template <class F, int LAYOUT, bool RS = false>
-__global__ void __launch_bounds__(256) k_trace(F f, const Img pool, const float4* __restrict__ rays,
+__global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __restrict__ rays,
                                                const uint32_t* __restrict__ order, uint64_t n,
                                                void* __restrict__ hits) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -761,7 +767,7 @@ __global__ void __launch_bounds__(256) k_trace(F f, const Img pool, const float4
 // counters in counters[0..2] (bytes of the format read, iterations, FP64
 // decisions), summed per warp then added atomically.
 template <class F, int LAYOUT, bool RS = false>
-__global__ void __launch_bounds__(256) k_trace_count(F f, const Img pool,
+__global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
                                                      const float4* __restrict__ rays, uint64_t n,
                                                      void* __restrict__ hits, unsigned long long* counters) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -972,7 +978,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
 }
 
 template <class F, int LAYOUT>
-__global__ void __launch_bounds__(256) k_render(F f, const Img pool, CamDev cam, uint64_t i0,
+__global__ void VX_PLAIN_BOUNDS k_render(F f, const Img pool, CamDev cam, uint64_t i0,
                                                 uint64_t n, void* __restrict__ hits) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
