@@ -75,9 +75,9 @@ def kernel_src_sha():
 
 
 def ncu_counters(kernel_key: str):
-    """(DRAM bytes, warp instructions) per launch of `kernel_key` from the
-    committed ncu summary, or (None, None) when the kernel source changed
-    since it was captured."""
+    """(DRAM bytes, warp instructions) per launch of `kernel_key`
+    ("trace:<format>:<kernel>") from the committed ncu summary, or
+    (None, None) when the kernel source changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(p):
         return None, None
@@ -236,7 +236,7 @@ def run_gpu(args):
     tuned = []
     if mode == vx.MODE_AUTO and not args.no_tune:
         for v in vols:
-            tuned.append(v.autotune(inc[: 1 << 19]))
+            tuned.append(v.autotune(inc))
 
     # --- algorithmic bytes per ray (instrumented kernels, outside timing) ---
     counts = {}
@@ -348,13 +348,15 @@ def run_gpu(args):
     alg_bytes = n_rays * (counts[dom]["node_bytes_per_ray"] + io)
     avg_ms = float(np.mean(ev[dom]))
     achieved = alg_bytes / (avg_ms / 1e3) / 1e9
-    kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}"
-    traffic, insts = ncu_counters(kernel_key)
     if name == "render":
         kname = "k_render"
     else:
         persistent = mode == vx.MODE_PERSISTENT or (mode == vx.MODE_AUTO and (not tuned or tuned[k]["mode"] == "persistent"))
         kname = "k_trace_persistent" if persistent else "k_trace"
+    # counters of the same kernel on the same format (a capture of another
+    # kernel does not count)
+    kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}:{kname}"
+    traffic, insts = ncu_counters(kernel_key)
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"{kname} {FORMATS[k]}",
@@ -431,7 +433,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"flushed before each step by a {FLUSH_BYTES >> 20} MiB write (inside the timed region)",
                        "hit_layout": "full 16 B",
-                       "mode": {"auto": "auto (vx_trace options autotuned per format on 2^19 of the rays)",
+                       "mode": {"auto": "auto (vx_trace options autotuned per format on the incoherent rays, outside the timed region)",
                                 "plain": "plain (one thread per ray)",
                                 "persistent": "persistent warps with ray refill"}[args.mode]},
             "plain_kernel_ms_per_step": round(plain_ms, 4) if plain_ms else None,
@@ -579,7 +581,7 @@ def run_formats512(args):
         v = vx.Volume(spec, grid)
         build_s = time.perf_counter() - t0
         st = v.stats()
-        tune = v.autotune(inc[: 1 << 19]) if not args.no_tune else None
+        tune = v.autotune(inc) if not args.no_tune else None
         ms_r = _timed(torch, lambda: v.render(cam, hp), args.steps, args.warmup)
         ms_t = _timed(torch, lambda: v.trace(inc, hi), args.steps, args.warmup)
         c = torch.zeros(3, dtype=torch.int64, device="cuda")

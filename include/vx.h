@@ -285,9 +285,11 @@ int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layou
 
 /* Picks vx_trace options for this volume: times candidates on `rays` (a
  * device sample of the rays the caller will trace, n of them) with CUDA
- * events on `stream` -- persistent refill threshold, iterations per refill
- * check, block size, coherence-sort granularity, plain vs persistent -- by
- * coordinate descent, and keeps the fastest; later vx_trace calls with
+ * events on `stream` (each candidate the best of three launches) --
+ * restarting vs stack traversal, top level in shared memory, coherence-sort
+ * granularity, persistent refill threshold, iterations per refill check,
+ * block size (two rounds), plain vs persistent -- by coordinate descent, and
+ * keeps the fastest; later vx_trace calls with
  * opts NULL or mode VX_MODE_AUTO use it.  Synchronises `stream`; allocates a
  * temporary n-hit buffer.  best (optional) receives the options, best_ms the
  * sample's time with them.  (Not in the paper: its formats are traced with

@@ -402,9 +402,13 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
         if (g > maxg) break;
         vx_trace_opts c = cur; c.sort_cell_log2 = g; consider(c);
     }
-    for (int r : {1, 4, 16, 24, 32}) { vx_trace_opts c = cur; c.refill = r; consider(c); }
-    for (int bu : {1, 2, 8, 16, 64}) { vx_trace_opts c = cur; c.burst = bu; consider(c); }
-    for (int bl : {64, 128}) { vx_trace_opts c = cur; c.block = bl; consider(c); }
+    // two rounds of coordinate descent over the persistent-kernel knobs (a
+    // knob's best value can move once the others have)
+    for (int round = 0; round < 2; round++) {
+        for (int r : {1, 2, 4, 8, 16, 24, 32}) { vx_trace_opts c = cur; c.refill = r; consider(c); }
+        for (int bu : {1, 2, 4, 8, 16, 32, 64}) { vx_trace_opts c = cur; c.burst = bu; consider(c); }
+        for (int bl : {64, 128, 256}) { vx_trace_opts c = cur; c.block = bl; consider(c); }
+    }
     { vx_trace_opts c = cur; c.mode = VX_MODE_PLAIN; consider(c); }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
