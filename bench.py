@@ -243,11 +243,11 @@ def run_gpu(args):
     prim_rays = vx.raygen_pinhole(cam)
     for k, v in enumerate(vols):
         for name, rays in (("render", prim_rays), ("trace", inc)):
-            c = torch.zeros(3, dtype=torch.int64, device="cuda")
+            c = torch.zeros(4, dtype=torch.int64, device="cuda")
             tmp = vx.alloc_hits(rays.shape[0])
             v.trace_counted(rays, tmp, c)
             torch.cuda.synchronize()
-            b, it, d = (int(x) for x in c.cpu())
+            b, it, d, _ = (int(x) for x in c.cpu())
             n = rays.shape[0]
             counts[(k, name)] = {"node_bytes_per_ray": b / n, "iters_per_ray": it / n, "fp64_per_ray": d / n}
     del prim_rays
@@ -584,10 +584,10 @@ def run_formats512(args):
         tune = v.autotune(inc) if not args.no_tune else None
         ms_r = _timed(torch, lambda: v.render(cam, hp), args.steps, args.warmup)
         ms_t = _timed(torch, lambda: v.trace(inc, hi), args.steps, args.warmup)
-        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        c = torch.zeros(4, dtype=torch.int64, device="cuda")
         v.trace_counted(inc, hi, c)
         torch.cuda.synchronize()
-        b, it, _ = (int(x) for x in c.cpu())
+        b, it, _, _ = (int(x) for x in c.cpu())
         per.append({"format": spec, "table2": LABEL.get(spec), "build_s": round(build_s, 2),
                     "device_bytes": st["device_bytes"], "canonical_bytes": st["canonical_bytes"],
                     "bytes_per_voxel": round(st["device_bytes"] / N_VOL ** 3, 5),

@@ -161,6 +161,22 @@ int vx_build(const char* spec, const vx_grid* grid, const vx_build_opts* opts, v
  * first).  NULL is accepted. */
 int vx_free(vx_volume v);
 
+/* A volume from a word buffer in the paper's layout (Sec. 3.3) -- e.g. one
+ * saved from vx_canonical -- for format `spec`; n_words >= 1, word 0 the root
+ * pointer.  The words are copied.  validate != 0 (the normal case) walks the
+ * whole buffer first: every pointer inside the buffer, octree masks
+ * consistent with their depth (leaf mask set exactly at the last depth),
+ * non-empty valid children, every DF distance equal to its definition;
+ * failure is VX_EINVAL with the offending word in vx_last_error().
+ * validate == 0 skips the walk and marks the volume unvalidated: every trace
+ * entry point then refuses it (VX_EINVAL) except vx_trace_counted, whose
+ * reads are checked.  opts as for vx_build (dedup_scope and threads unused).
+ * Stats: canonical_words and per-level words / node counts (from the walk),
+ * occupied_voxels 0.  The paper has no loader: its construction writes the
+ * buffer to a file (Sec. 4.1); this reads such a buffer back. */
+int vx_load(const char* spec, const uint32_t* words, uint64_t n_words, const vx_build_opts* opts, int32_t validate,
+            vx_volume* out);
+
 /* Size and build statistics of a volume.  Level k counts the words written
  * for its structures (Raw arrays, octree node lists, DAG nodes) and its
  * nodes: Raw sub-volumes, or octree / DAG nodes including leaf nodes. */
@@ -250,12 +266,16 @@ int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hi
              const vx_trace_opts* opts, void* stream);
 
 /* Same results as vx_trace from an instrumented kernel that also adds, over
- * all rays, into the device array counters[0..2] (caller-zeroed, 8-byte
+ * all rays, into the device array counters[0..3] (caller-zeroed, 8-byte
  * aligned, unsigned 64-bit): [0] bytes of the format read by the traversal
- * (Raw cell 4, octree node 8, DAG mask 4 + pointer 4, leaf terminating
- * integer 4), [1] loop iterations, [2] decisions re-taken in FP64.  For
- * measurement: the bytes a ray must read from the format are the
- * algorithmic traffic of the method. */
+ * (Raw cell 4, DF cell 8, octree node 8, DAG mask 4 + pointer 4, leaf
+ * terminating integer 4), [1] loop iterations, [2] decisions re-taken in
+ * FP64, [3] reads refused because they fell outside the volume's words.
+ * For measurement: the bytes a ray must read from the format are the
+ * algorithmic traffic of the method.  This kernel checks every read of the
+ * volume against its size: a refused read counts in [3] and the ray's hit
+ * reports VX_STATUS_ERROR, so it is the one trace that may read a volume
+ * loaded without validation (vx_load). */
 int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
                      const vx_trace_opts* opts, void* stream, unsigned long long* counters);
 

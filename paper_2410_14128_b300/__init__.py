@@ -84,6 +84,8 @@ _SIGS = {
     "vx_build": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_Grid), ctypes.POINTER(_BuildOpts),
                                 ctypes.POINTER(ctypes.c_void_p)]),
     "vx_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "vx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(_BuildOpts),
+                               ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "vx_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Stats)]),
     "vx_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint64)]),
     "vx_decode_brick": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
@@ -239,6 +241,36 @@ class Volume:
         self.log2_dim = tuple(dims)
         self._keep = []
 
+    @classmethod
+    def load(cls, spec: str, words: np.ndarray, *, validate: bool = True, device: int = -1, upload: bool = True,
+             canonical_device: bool = False) -> "Volume":
+        """A volume from a word buffer in the paper's layout (e.g. `canonical()`
+        of another volume, or `words` of a file written by `save`).  With
+        validate=False only `trace_counted` may trace it (its reads are
+        checked)."""
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        self = cls.__new__(cls)
+        self._keep = []
+        o = _BuildOpts(DEDUP_WHOLE_LEVEL, device, 0 if upload else 1, 0, 1 if canonical_device else 0)
+        h = ctypes.c_void_p()
+        _check(lib().vx_load(spec.encode(), ctypes.c_void_p(w.ctypes.data), w.size, ctypes.byref(o), int(validate),
+                             ctypes.byref(h)))
+        self._h = h
+        self.spec = spec
+        (lx, ly, lz) = self.stats()["log2_dim"]
+        self.log2_dim = (lx, ly, lz)
+        return self
+
+    def save(self, path: str):
+        """Writes the spec and the canonical words (numpy .npz); `Volume.load`
+        of them gives the same volume."""
+        np.savez(path, spec=np.array(self.spec), words=self.canonical())
+
+    @classmethod
+    def open(cls, path: str, **kw) -> "Volume":
+        with np.load(path) as z:
+            return cls.load(str(z["spec"]), z["words"], **kw)
+
     # -- lifetime ---------------------------------------------------------
     def free(self):
         if getattr(self, "_h", None):
@@ -295,8 +327,8 @@ class Volume:
         return hits
 
     def trace_counted(self, rays, hits, counters, layout: int = HIT_FULL, stream=None, **opts):
-        """As trace(), adding [bytes read, iterations, FP64 decisions] into
-        `counters` (CUDA int64 tensor of 3, caller-zeroed)."""
+        """As trace(), adding [bytes read, iterations, FP64 decisions, reads
+        refused] into `counters` (CUDA int64 tensor of 4, caller-zeroed)."""
         n = rays.shape[0]
         o = _opts(**opts)
         _check(lib().vx_trace_counted(self._h, ctypes.c_void_p(rays.data_ptr()), n, ctypes.c_void_p(hits.data_ptr()),

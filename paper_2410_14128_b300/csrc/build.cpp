@@ -301,6 +301,8 @@ struct WriteRec {
     uint8_t tag, level;
 };
 
+}  // namespace
+
 // L1 distance transform of a W x H x D grid of cells, capped at M: d = 0 on
 // non-empty cells, else min(M, distance to the nearest non-empty cell).  The
 // L1 metric separates by axis, so a forward and a backward sweep along x,
@@ -323,6 +325,8 @@ void l1_distance(const uint32_t* terms, const int e[3], uint32_t M, std::vector<
             }
     }
 }
+
+namespace {
 
 // Interleaves terminating integers and distances into a DF sub-volume.
 void df_words(const std::vector<uint32_t>& terms, const int e[3], uint32_t M, std::vector<uint32_t>& out) {

@@ -48,9 +48,14 @@ class DeviceScope {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-int check_trace_args(vx_volume v, const void* rays, uint64_t n, const void* hits, int32_t layout) {
+// checked: the caller is the instrumented trace, whose reads are checked
+// against the image size, so it may read a volume loaded without validation.
+int check_trace_args(vx_volume v, const void* rays, uint64_t n, const void* hits, int32_t layout,
+                     bool checked = false) {
     if (!v) return fail(VX_EINVAL, "volume is NULL");
     if (!v->v.d_pool) return fail(VX_EINVAL, "volume has no device image (built with no_upload)");
+    if (v->v.unvalidated && !checked)
+        return fail(VX_EINVAL, "volume was loaded without validation: only vx_trace_counted may trace it");
     if (layout != VX_HIT_FULL && layout != VX_HIT_COMPACT) return fail(VX_EINVAL, "bad hit layout %d", layout);
     if (layout == VX_HIT_COMPACT && v->v.spec.ldim[0] + v->v.spec.ldim[1] + v->v.spec.ldim[2] >= 32)
         return fail(VX_EINVAL, "compact hits need fewer than 2^32 voxels");
@@ -146,6 +151,35 @@ int pipeline(Volume& V, uint64_t n, void* stream, Work work) {
 
 }  // namespace
 
+namespace {
+// Device image (packed when allowed and possible) and queue counters.
+int upload(Volume& V, const vx_build_opts& o, bool allow_packed) {
+    int dev = o.device;
+    if (dev < 0) {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e) return cuda_fail(e, "cudaGetDevice");
+    }
+    DeviceScope ds(dev);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    V.device = dev;
+    const uint64_t bytes = V.built.words.size() * sizeof(uint32_t);
+    std::vector<uint32_t> packed;
+    const bool use_packed = allow_packed && pack_device_image(V.spec, V.built.words, packed);
+    V.packed = use_packed ? 1 : 0;
+    const uint32_t* src_words = use_packed ? packed.data() : V.built.words.data();
+    cudaError_t e = cudaMalloc((void**)&V.d_pool, bytes);
+    if (e) return cuda_fail(e, "cudaMalloc (device image)");
+    e = cudaMemcpy(V.d_pool, src_words, bytes, cudaMemcpyHostToDevice);
+    if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
+    V.pool_words = V.built.words.size();
+    e = cudaMalloc((void**)&V.d_queue, kQueueRing * sizeof(unsigned long long));
+    if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMalloc (queue counters)"); }
+    V.stats.device_bytes = bytes;
+    V.stats.packed = V.packed;
+    return VX_OK;
+}
+}  // namespace
+
 extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_opts* opts, vx_volume* out) {
     clear_error();
     if (!out) return fail(VX_EINVAL, "out is NULL");
@@ -195,28 +229,55 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
     st.specialized = kernel_set_specialized(V.kernels) ? 1 : 0;
 
     if (!o.no_upload) {
-        int dev = o.device;
-        if (dev < 0) {
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e) return cuda_fail(e, "cudaGetDevice");
-        }
-        DeviceScope ds(dev);
-        if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
-        V.device = dev;
-        const uint64_t bytes = V.built.words.size() * sizeof(uint32_t);
-        std::vector<uint32_t> packed;
-        const bool use_packed = !o.canonical_device && pack_device_image(sp, V.built.words, packed);
-        V.packed = use_packed ? 1 : 0;
-        const uint32_t* src_words = use_packed ? packed.data() : V.built.words.data();
-        cudaError_t e = cudaMalloc((void**)&V.d_pool, bytes);
-        if (e) return cuda_fail(e, "cudaMalloc (device image)");
-        e = cudaMemcpy(V.d_pool, src_words, bytes, cudaMemcpyHostToDevice);
-        if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
-        V.pool_words = V.built.words.size();
-        e = cudaMalloc((void**)&V.d_queue, kQueueRing * sizeof(unsigned long long));
-        if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMalloc (queue counters)"); }
-        st.device_bytes = bytes;
-        st.packed = V.packed;
+        rc = upload(V, o, !o.canonical_device);
+        if (rc) return rc;
+        st.upload_ms = now_ms() - t1;
+    }
+    *out = h.release();
+    return VX_OK;
+}
+
+extern "C" int vx_load(const char* spec, const uint32_t* words, uint64_t n_words, const vx_build_opts* opts,
+                       int32_t validate, vx_volume* out) {
+    clear_error();
+    if (!out) return fail(VX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!words || n_words == 0) return fail(VX_EINVAL, "words is empty");
+    if (n_words > 0xFFFFFFFFull) return fail(VX_ETOOBIG, "buffer exceeds 2^32 words (16 GiB, Sec. 3.3)");
+    Spec sp;
+    int rc = parse_spec(spec, &sp);
+    if (rc) return rc;
+    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, {0, 0, 0}};
+    if (opts) o = *opts;
+    std::unique_ptr<vx_volume_s> h(new vx_volume_s);
+    Volume& V = h->v;
+    V.spec = sp;
+    const double t0 = now_ms();
+    V.built.words.assign(words, words + n_words);
+    if (validate) {
+        rc = validate_canonical(sp, V.built.words.data(), n_words, &V.built);
+        if (rc) return rc;
+    } else {
+        V.unvalidated = true;
+    }
+    vx_stats& st = V.stats;
+    memset(&st, 0, sizeof st);
+    st.n_levels = (uint32_t)sp.lv.size();
+    st.n_node_levels = sp.fmt.J;
+    for (int i = 0; i < 3; i++) st.log2_dim[i] = (uint32_t)sp.ldim[i];
+    st.canonical_words = n_words;
+    for (int k = 0; k < VX_MAX_LEVELS; k++) {
+        st.level_words[k] = V.built.level_words[k];
+        st.level_nodes[k] = V.built.level_nodes[k];
+    }
+    st.build_ms = now_ms() - t0;
+    V.kernels = kernels_for(sp);
+    st.specialized = kernel_set_specialized(V.kernels) ? 1 : 0;
+    if (!o.no_upload) {
+        const double t1 = now_ms();
+        // an unvalidated buffer is uploaded as it is: the packer trusts the layout
+        rc = upload(V, o, validate && !o.canonical_device);
+        if (rc) return rc;
         st.upload_ms = now_ms() - t1;
     }
     *out = h.release();
@@ -284,7 +345,7 @@ extern "C" int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits,
 extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
                                 const vx_trace_opts* opts, void* stream, unsigned long long* counters) {
     clear_error();
-    int rc = check_trace_args(v, rays, n, hits, hit_layout);
+    int rc = check_trace_args(v, rays, n, hits, hit_layout, true);
     if (!rc) rc = check_opts(opts);
     if (rc || n == 0) return rc;
     if ((rc = check_ptrs(rays, hits, hit_layout))) return rc;

@@ -169,10 +169,10 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
         const int smem_top = o ? o->smem_top : 0;
-        e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits,
+        e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), order, n, hits,
                                         layout, block, bps, refill, burst, restart, smem_top, st, next);
     } else {
-        e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
+        e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
                              block, restart, st);
     }
     if (scratch) cudaFreeAsync(scratch, st);
@@ -184,7 +184,7 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
                        const vx_trace_opts* o, void* stream, unsigned long long* counters) {
     const int block = pick_block(o);
     const int restart = o ? o->restart : 0;
-    int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed}, reinterpret_cast<const float4*>(rays), n, hits, layout,
+    int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), n, hits, layout,
                                    block, restart, (cudaStream_t)stream, counters);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
@@ -200,10 +200,10 @@ int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t
         if (!next) return fail(VX_ECUDA, "no queue counter for the persistent kernel");
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
-        e = v.kernels->render_persistent(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block,
+        e = v.kernels->render_persistent(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, to_dev(cp), i0, n, hits, layout, block,
                                          refill, burst, (cudaStream_t)stream, next);
     } else {
-        e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed}, to_dev(cp), i0, n, hits, layout, block,
+        e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, to_dev(cp), i0, n, hits, layout, block,
                               (cudaStream_t)stream);
     }
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));

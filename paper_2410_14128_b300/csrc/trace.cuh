@@ -151,6 +151,7 @@ struct HitRec {
 // read (in bytes), loop iterations, and decisions re-taken in FP64.
 struct Cnt {
     uint32_t bytes = 0, iters = 0, fp64 = 0;
+    uint32_t refused = 0;  // reads outside the image, refused (instrumented kernels check every read)
 };
 
 __device__ __forceinline__ HitRec miss_rec(uint32_t st) {
@@ -263,6 +264,7 @@ __device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint3
 struct Img {
     const uint32_t* w;
     int packed;
+    uint32_t n;  // words in the image (the instrumented kernels check every read against it)
 };
 constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 
@@ -311,7 +313,19 @@ struct Walker {
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
     uint2* S;         // this thread's node stack, F::kMaxJ entries (owned by the caller)
+    uint32_t lim;     // words in the image (checked by the instrumented walker)
     Cnt cnt;
+
+    // A word of the image.  The instrumented walker (COUNT) checks every
+    // index against the image size and refuses reads outside it (counted; the
+    // ray then reports ST_ERROR), so it can walk a buffer nobody validated.
+    __device__ __forceinline__ uint32_t rd(const uint32_t* __restrict__ pool, uint32_t i) {
+        if (COUNT && i >= lim) {
+            cnt.refused++;
+            return 0u;
+        }
+        return ldw(pool, i);
+    }
 
     __device__ __forceinline__ void load_level(const F& f) {
         kind_c = f.kind(j);
@@ -339,13 +353,13 @@ struct Walker {
             const uint32_t rank = __popc(m & ((1u << idx) - 1u));
             if (svo) {
                 const uint32_t a = p + 2u * rank;
-                p = ldw(pool, a);
-                m = ldw(pool, a + 1) & 0xFFu;
+                p = rd(pool, a);
+                m = rd(pool, a + 1) & 0xFFu;
                 VX_CNT(bytes, 8);
             } else {
-                const uint32_t cp = ldw(pool, p + 1u + rank);
+                const uint32_t cp = rd(pool, p + 1u + rank);
                 if (im.packed) { p = cp & kPtrMask; m = cp >> 24; VX_CNT(bytes, 4); }
-                else { p = cp; m = ldw(pool, cp) & 0xFFu; VX_CNT(bytes, 8); }
+                else { p = cp; m = rd(pool, cp) & 0xFFu; VX_CNT(bytes, 8); }
             }
         }
         Pc = p;
@@ -357,6 +371,7 @@ struct Walker {
 
     __device__ __forceinline__ bool start(const F& f, const Img im, const RayIn& ray, HitRec& out) {
         const uint32_t* __restrict__ pool = im.w;
+        lim = im.n;
         r = ray;
         // Invalid rays: any NaN, or an infinite tmin.
         if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
@@ -445,7 +460,7 @@ struct Walker {
         }
 
         // ---- root node ----
-        const uint32_t root = ldw(pool, 0);
+        const uint32_t root = rd(pool, 0);
         VX_CNT(bytes, 4);
         if (root == 0) {
             out = miss_rec(ST_MISS);
@@ -454,9 +469,9 @@ struct Walker {
         {
             const int k0 = f.kind(0);
             if (k0 == K_RAW || k0 == K_DF) { Pc = root; Mc = 0; }
-            else if (k0 == K_SVO) { Pc = ldw(pool, root); Mc = ldw(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+            else if (k0 == K_SVO) { Pc = rd(pool, root); Mc = rd(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
             else if (im.packed) { Pc = root & kPtrMask; Mc = root >> 24; }
-            else { Pc = root; Mc = ldw(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
+            else { Pc = root; Mc = rd(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
         }
         j = 0;
         S[0] = make_uint2(Pc, Mc);
@@ -594,8 +609,8 @@ struct Walker {
         const uint32_t as = is_df ? 2u * idx : idx;  // word of the cell in a staged top level
         const bool staged = TOPS && j == 0;
         uint32_t w = 0, dist = 0;
-        if (is_raw || df_read) w = staged ? vx_top_smem[as] : ldw(pool, a);
-        if (df_read) dist = staged ? vx_top_smem[as + 1] : ldw(pool, a + 1);  // same sector as the cell word
+        if (is_raw || df_read) w = staged ? vx_top_smem[as] : rd(pool, a);
+        if (df_read) dist = staged ? vx_top_smem[as + 1] : rd(pool, a + 1);  // same sector as the cell word
         VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
         const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;
         if (is_df) skip = df_read ? (occ ? 0 : (int)dist - 1) : skip - 1;
@@ -607,17 +622,17 @@ struct Walker {
                 const uint32_t rank = __popc(Mc & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = Pc + 2u * rank;
-                    if (bot_c) { term = ldw(pool, addr); VX_CNT(bytes, 4); }
-                    else { Pn = ldw(pool, addr); Mn = ldw(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
+                    if (bot_c) { term = rd(pool, addr); VX_CNT(bytes, 4); }
+                    else { Pn = rd(pool, addr); Mn = rd(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
-                    const uint32_t cp = ldw(pool, Pc + 1u + rank);
+                    const uint32_t cp = rd(pool, Pc + 1u + rank);
                     if (im.packed) {
                         if (bot_c) term = cp;
                         else { Pn = cp & kPtrMask; Mn = cp >> 24; node_ready = true; }
                         VX_CNT(bytes, 4);
                     } else {
-                        if (bot_c) term = ldw(pool, cp);
-                        else { Pn = cp; Mn = ldw(pool, cp) & 0xFFu; node_ready = true; }
+                        if (bot_c) term = rd(pool, cp);
+                        else { Pn = cp; Mn = rd(pool, cp) & 0xFFu; node_ready = true; }
                         VX_CNT(bytes, 8);
                     }
                 }
@@ -633,9 +648,9 @@ struct Walker {
             if (!node_ready) {
                 const int nk = f.kind(j + 1);
                 if (nk == K_RAW || nk == K_DF) { Pn = term; }
-                else if (f.has_svo() && nk == K_SVO) { Pn = ldw(pool, term); Mn = ldw(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
+                else if (f.has_svo() && nk == K_SVO) { Pn = rd(pool, term); Mn = rd(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
                 else if (im.packed) { Pn = term & kPtrMask; Mn = term >> 24; }
-                else { Pn = term; Mn = ldw(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
+                else { Pn = term; Mn = rd(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
             if (!RESTART || ((f.top() >> j) & 1u)) S[j] = make_uint2(Pn, Mn);
@@ -686,6 +701,8 @@ __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const Ra
         cnt.bytes += w.cnt.bytes;
         cnt.iters += w.cnt.iters;
         cnt.fp64 += w.cnt.fp64;
+        cnt.refused += w.cnt.refused;
+        if (w.cnt.refused) h = miss_rec(ST_ERROR);
     }
     return h;
 }
@@ -764,8 +781,9 @@ __global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __res
 }
 
 // Instrumented twin of k_trace: same results, plus totals of the per-ray
-// counters in counters[0..2] (bytes of the format read, iterations, FP64
-// decisions), summed per warp then added atomically.
+// counters in counters[0..3] (bytes of the format read, iterations, FP64
+// decisions, reads refused as outside the image), summed per warp then added
+// atomically.  Every read of the image is checked against its size.
 template <class F, int LAYOUT, bool RS = false>
 __global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
                                                      const float4* __restrict__ rays, uint64_t n,
@@ -777,16 +795,18 @@ __global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
         const HitRec h = trace_ray<true, F, RS>(f, pool, r, cnt);
         store_hit<LAYOUT>(f, hits, i, h);
     }
-    unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64;
+    unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64, rf = cnt.refused;
     for (int o = 16; o > 0; o >>= 1) {
         b += __shfl_down_sync(0xffffffffu, b, o);
         it += __shfl_down_sync(0xffffffffu, it, o);
         d += __shfl_down_sync(0xffffffffu, d, o);
+        rf += __shfl_down_sync(0xffffffffu, rf, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(counters + 0, b);
         atomicAdd(counters + 1, it);
         atomicAdd(counters + 2, d);
+        atomicAdd(counters + 3, rf);
     }
 }
 

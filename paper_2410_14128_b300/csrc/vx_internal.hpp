@@ -78,6 +78,14 @@ struct BuildResult {
 // top level and a thread-safe source, and gives the same words as the sequential.
 int build_canonical(const Spec& spec, VoxelSource& src, int dedup_scope, BuildResult* out, int threads);
 
+// L1 distance of every cell of a W x H x D grid (terms != 0 are non-empty) to
+// the nearest non-empty cell, capped at M (the DF level of Table 1).
+void l1_distance(const uint32_t* terms, const int e[3], uint32_t M, std::vector<uint32_t>& d);
+
+// Checks a word buffer against the layout of `spec` (pointers inside the
+// buffer, masks, DF distances); fills the per-level word and node counts.
+int validate_canonical(const Spec& spec, const uint32_t* words, uint64_t n, BuildResult* stats);
+
 // Device image in the packed layout (same offsets); false when the volume is
 // too large for it or has no SVDAG level (then the canonical words are used).
 bool pack_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out);
@@ -123,6 +131,7 @@ struct Volume {
     uint32_t* d_pool = nullptr;
     uint64_t pool_words = 0;
     int packed = 0;  // device image in the packed layout (pack.cpp)
+    bool unvalidated = false;  // loaded without validation: only the checked (counted) trace may read it
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
     Staging staging;

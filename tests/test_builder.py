@@ -248,3 +248,63 @@ def test_df_cap_closed_form():
         d = w[1 + 1::2][: 16 ** 3].reshape(16, 16, 16)
         z, y, x = np.indices((16, 16, 16))
         assert np.array_equal(d, np.minimum(x + y + z, M)), M
+
+
+# ---------------------------------------------------------------------------
+# vx_load: word buffers validated against the layout, save / open round trip
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", ["R(2,2,2) S(1) G(1)", "D(2,2,2,3) R(2,2,2)", "S(2) G(2)", "G(4)", "R(1,1,1) S(1) G(2)"])
+def test_load_validated_roundtrip(spec, tmp_path):
+    g = synth.random_grid(51, (16, 16, 16), 0.15, colors=3)
+    v = build(spec, g)
+    w = v.canonical()
+    u = vx.Volume.load(spec, w, upload=False)
+    assert np.array_equal(u.canonical(), w)
+    a, b = v.stats(), u.stats()
+    assert a["canonical_words"] == b["canonical_words"]
+    assert a["level_words"] == b["level_words"] and a["level_nodes"] == b["level_nodes"]
+    assert np.array_equal(u.decode_brick(0, 0, 0, 4), g)
+    v.save(str(tmp_path / "vol.npz"))
+    r = vx.Volume.open(str(tmp_path / "vol.npz"), upload=False)
+    assert r.spec == spec and np.array_equal(r.canonical(), w)
+
+
+@pytest.mark.parametrize("ex", _layout(), ids=lambda e: e["name"])
+def test_load_accepts_hand_built_buffers(ex):
+    w = np.zeros(ex["nwords"], np.uint32)
+    for k, val in ex["set"].items():
+        w[int(k)] = val
+    vx.Volume.load(ex["spec"], w, upload=False)
+
+
+def _malformed():
+    with open(os.path.join(GOLDEN, "layout_examples.json")) as f:
+        return json.load(f)["malformed"]
+
+
+@pytest.mark.parametrize("ex", _malformed(), ids=lambda e: e["name"])
+def test_load_rejects_malformed_buffers(ex):
+    w = np.zeros(ex["nwords"], np.uint32)
+    for k, val in ex["set"].items():
+        w[int(k)] = val
+    with pytest.raises(vx.VxError) as e:
+        vx.Volume.load(ex["spec"], w, upload=False)
+    assert e.value.code == vx.VX_EINVAL
+    vx.Volume.load(ex["spec"], w, upload=False, validate=False)  # the walk is skipped
+
+
+def test_load_rejects_corruption_anywhere():
+    g = synth.terrain_volume(52, 32)
+    spec = "R(2,2,2) S(1) G(2)"
+    w = build(spec, g).canonical()
+    rng = np.random.default_rng(53)
+    rejected = 0
+    for _ in range(40):
+        bad = w.copy()
+        i = int(rng.integers(1, len(w)))
+        bad[i] = np.uint32(len(w) + int(rng.integers(1, 1 << 20)))  # a pointer past the end, or a wrong word
+        try:
+            vx.Volume.load(spec, bad, upload=False)
+        except vx.VxError:
+            rejected += 1
+    assert rejected >= 20  # most corruptions hit a pointer or a mask; RGBA words may take any value

@@ -431,7 +431,7 @@ def test_restart_equals_stack(spec, canonical):
     r = torch.from_numpy(rays).cuda()
     counts = []
     for restart in (False, True):
-        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        c = torch.zeros(4, dtype=torch.int64, device="cuda")
         h = vx.alloc_hits(len(rays))
         vol.trace_counted(r, h, c, restart=restart)
         torch.cuda.synchronize()
@@ -488,7 +488,7 @@ def test_df_walks_the_same_cells_as_raw(df, raw):
     out = {}
     for spec in (df, raw):
         vol = vx.Volume(spec, g)
-        c = torch.zeros(3, dtype=torch.int64, device="cuda")
+        c = torch.zeros(4, dtype=torch.int64, device="cuda")
         h = vx.alloc_hits(len(rays))
         vol.trace_counted(r, h, c)
         torch.cuda.synchronize()
@@ -534,3 +534,59 @@ def test_smem_top_equals_plain(spec):
             assert np.array_equal(got, ref), (block, refill, burst, rep)
     with pytest.raises(vx.VxError):
         gpu_trace(vol, rays, smem_top=2)
+
+
+# ---------------------------------------------------------------------------
+# Volumes from word buffers (vx_load); the checked trace on corrupt buffers
+# ---------------------------------------------------------------------------
+def _counted(vol, rays, **opts):
+    r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
+    c = torch.zeros(4, dtype=torch.int64, device="cuda")
+    h = vx.alloc_hits(len(rays))
+    vol.trace_counted(r, h, c, **opts)
+    torch.cuda.synchronize()
+    return vx.hits_to_numpy(h), [int(x) for x in c.cpu()]
+
+
+@pytest.mark.parametrize("canonical", [False, True])
+def test_loaded_volume_traces_like_the_built_one(canonical):
+    g = synth.terrain_volume(131, 128)
+    rays = np.concatenate([synth.incoherent_rays(132, 128, 50001), synth.box_rays(133, 128, 40, 10000)])
+    for spec in ["R(3,3,3) S(2) G(2)", "D(3,3,3,6) G(4)", "R(2,2,2) R(2,2,2) R(3,3,3)"]:
+        built = vx.Volume(spec, g)
+        ref = gpu_trace(built, rays)
+        loaded = vx.Volume.load(spec, built.canonical(), canonical_device=canonical)
+        assert loaded.stats()["packed"] == built.stats()["packed"] or canonical
+        assert np.array_equal(gpu_trace(loaded, rays), ref), spec
+        assert np.array_equal(gpu_trace(loaded, rays, mode=vx.MODE_PERSISTENT), ref), spec
+
+
+def test_checked_trace_refuses_reads_outside_a_corrupt_buffer():
+    g = synth.terrain_volume(134, 128)
+    spec = "R(3,3,3) S(2) G(2)"
+    built = vx.Volume(spec, g)
+    w = built.canonical()
+    rays = np.concatenate([synth.incoherent_rays(135, 128, 50001), synth.box_rays(136, 128, 40, 10000)])
+    ref = gpu_trace(built, rays)
+    # a valid buffer loaded without validation: only the checked trace may read it, and it finds nothing wrong
+    u = vx.Volume.load(spec, w, validate=False)
+    with pytest.raises(vx.VxError):
+        gpu_trace(u, rays)
+    with pytest.raises(vx.VxError):
+        gpu_trace(u, rays, mode=vx.MODE_PERSISTENT)
+    h, c = _counted(u, rays)
+    assert c[3] == 0 and np.array_equal(h, ref)
+    # corrupt pointers in the top level and in the octree below: reads past the end are refused
+    bad = w.copy()
+    root = int(w[0])
+    cells = root + np.nonzero(w[root:root + 512])[0]
+    rng = np.random.default_rng(137)
+    bad[rng.choice(cells, 40, replace=False)] = np.uint32(0xFFFFFF00)
+    bad[rng.choice(np.arange(1, root), 200, replace=False)] = np.uint32(len(w) + 12345)  # words below the root (post-order)
+    v2 = vx.Volume.load(spec, bad, validate=False)
+    for restart in (False, True):
+        h2, c2 = _counted(v2, rays, restart=restart)
+        st = h2["status"]
+        assert c2[3] > 0
+        assert set(np.unique(st).tolist()) <= {vx.STATUS_MISS, vx.STATUS_HIT, vx.STATUS_ERROR}
+        assert (st == vx.STATUS_ERROR).sum() > 0
