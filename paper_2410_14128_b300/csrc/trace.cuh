@@ -308,8 +308,6 @@ struct Walker {
     int v0[3], c[3];
     int j, la, lp, budget;
     int skip;  // DF level: cells the walk may still enter without a look-up
-    int kind_c, s_c, b_c[3];  // node level j: kind, children side, fanout (cached)
-    bool bot_c;
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
     uint2* S;         // this thread's node stack, F::kMaxJ entries (owned by the caller)
@@ -327,13 +325,15 @@ struct Walker {
         return ldw(pool, i);
     }
 
-    __device__ __forceinline__ void load_level(const F& f) {
-        kind_c = f.kind(j);
-        s_c = f.s(j);
-        bot_c = f.bot(j);
-        if (j == 0) { b_c[0] = f.b0(0); b_c[1] = f.b0(1); b_c[2] = f.b0(2); }
-        else { b_c[0] = b_c[1] = b_c[2] = f.b(j); }
-    }
+
+    // Node level j: kind, children side (log2 voxels), fanout per axis, and
+    // whether its children are terminating integers -- extracted from the
+    // format's constants each time (measured: cheaper than keeping copies in
+    // registers, which spill).
+    __device__ __forceinline__ int lk(const F& f) const { return f.kind(j); }
+    __device__ __forceinline__ int ls(const F& f) const { return f.s(j); }
+    __device__ __forceinline__ int lb(const F& f, int a) const { return j == 0 ? f.b0(a) : f.b(j); }
+    __device__ __forceinline__ bool lbot(const F& f) const { return f.bot(j); }
 
     // Node of level j reached from the root of its format level: the nodes
     // on the way are ancestors of the cell the walk just left, so each exists.
@@ -495,7 +495,6 @@ struct Walker {
         // A ray crosses at most nx + ny + nz cells of any level and each step
         // costs at most J descents; past this bound the ray reports ST_ERROR.
         budget = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (f.J() + 2);
-        load_level(f);
         skip = 0;
         return false;
     }
@@ -513,7 +512,7 @@ struct Walker {
         float tn[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << s_c;
+            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << ls(f);
             tn[i] = sg[i] != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
         }
         int a = tn[1] < tn[0] ? 1 : 0;
@@ -553,7 +552,7 @@ struct Walker {
         la = a;
         lp = pla;
         fresh = false;
-        const int h = 31 - __clz((uint32_t)(old ^ nw)) + s_c;  // highest changed voxel-coordinate bit
+        const int h = 31 - __clz((uint32_t)(old ^ nw)) + ls(f);  // highest changed voxel-coordinate bit
         const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
         if (h >= span) {
             skip = 0;  // the distances are those of the node the walk left
@@ -562,7 +561,7 @@ struct Walker {
                 return true;
             }
             const int jp = f.jpop(h);
-            const int sh = f.s(jp) - s_c;
+            const int sh = f.s(jp) - ls(f);
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] >>= sh;
             j = jp;
@@ -573,7 +572,6 @@ struct Walker {
                 Pc = e.x;
                 Mc = e.y;
             }
-            load_level(f);
         }
         return false;
     }
@@ -586,8 +584,8 @@ struct Walker {
         }
         VX_CNT(iters, 1);
         const int J = f.J();
-        const int kind = kind_c;
-        const int bx = b_c[0], by = b_c[1], bz = b_c[2];
+        const int kind = lk(f);
+        const int bx = lb(f, 0), by = lb(f, 1), bz = lb(f, 2);
         const uint32_t lx = (uint32_t)c[0] & ((1u << bx) - 1u);
         const uint32_t ly = (uint32_t)c[1] & ((1u << by) - 1u);
         const uint32_t lz = (uint32_t)c[2] & ((1u << bz) - 1u);
@@ -622,16 +620,16 @@ struct Walker {
                 const uint32_t rank = __popc(Mc & ((1u << idx) - 1u));
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = Pc + 2u * rank;
-                    if (bot_c) { term = rd(pool, addr); VX_CNT(bytes, 4); }
+                    if (lbot(f)) { term = rd(pool, addr); VX_CNT(bytes, 4); }
                     else { Pn = rd(pool, addr); Mn = rd(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
                     const uint32_t cp = rd(pool, Pc + 1u + rank);
                     if (im.packed) {
-                        if (bot_c) term = cp;
+                        if (lbot(f)) term = cp;
                         else { Pn = cp & kPtrMask; Mn = cp >> 24; node_ready = true; }
                         VX_CNT(bytes, 4);
                     } else {
-                        if (bot_c) term = rd(pool, cp);
+                        if (lbot(f)) term = rd(pool, cp);
                         else { Pn = cp; Mn = rd(pool, cp) & 0xFFu; node_ready = true; }
                         VX_CNT(bytes, 8);
                     }
@@ -656,8 +654,7 @@ struct Walker {
             if (!RESTART || ((f.top() >> j) & 1u)) S[j] = make_uint2(Pn, Mn);
             Pc = Pn;
             Mc = Mn;
-            load_level(f);
-            const int sn = s_c, bn = b_c[0];
+            const int sn = ls(f), bn = lb(f, 0);
             const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
 #pragma unroll
             for (int i = 0; i < 3; i++) {
