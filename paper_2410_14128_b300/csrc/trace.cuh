@@ -304,7 +304,7 @@ struct Walker {
     float tx, tcur;
     float gabs;  // guard band: 2^-20 of the largest |t| this walk compares
     float gpos;  // guard band for positions o + t d inside the grid
-    int sg[3];
+    // (direction sign per axis, -1 / 0 / 1: sgn(), from the ray)
     int v0[3], c[3];
     int j, la, lp, budget;
     int skip;  // DF level: cells the walk may still enter without a look-up
@@ -334,6 +334,11 @@ struct Walker {
     __device__ __forceinline__ int ls(const F& f) const { return f.s(j); }
     __device__ __forceinline__ int lb(const F& f, int a) const { return j == 0 ? f.b0(a) : f.b(j); }
     __device__ __forceinline__ bool lbot(const F& f) const { return f.bot(j); }
+
+    __device__ __forceinline__ int sgn(int i) const {
+        const float d = sel3(r.d, i);
+        return d > 0.0f ? 1 : (d < 0.0f ? -1 : 0);
+    }
 
     // Node of level j reached from the root of its format level: the nodes
     // on the way are ancestors of the cell the walk just left, so each exists.
@@ -382,7 +387,6 @@ struct Walker {
         float nf[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            sg[i] = r.d[i] > 0.0f ? 1 : (r.d[i] < 0.0f ? -1 : 0);
             inv[i] = __frcp_rn(r.d[i]);
             nf[i] = (float)(1 << f.ldim(i));
         }
@@ -394,15 +398,15 @@ struct Walker {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             t0[i] = 0.0f;
-            if (sg[i] == 0) {
+            if (sgn(i) == 0) {
                 if (!(r.o[i] >= 0.0f && r.o[i] < nf[i])) {
                     out = miss_rec(ST_MISS);
                     return true;
                 }
                 continue;
             }
-            const float lo = sg[i] > 0 ? 0.0f : nf[i];
-            const float hi = sg[i] > 0 ? nf[i] : 0.0f;
+            const float lo = sgn(i) > 0 ? 0.0f : nf[i];
+            const float hi = sgn(i) > 0 ? nf[i] : 0.0f;
             t0[i] = (lo - r.o[i]) * inv[i];
             const float t1 = (hi - r.o[i]) * inv[i];
             if (t0[i] > best) { best = t0[i]; e = i; }
@@ -411,7 +415,7 @@ struct Walker {
         bool unsure = false;
 #pragma unroll
         for (int i = 0; i < 3; i++)
-            if (sg[i] != 0 && i != e && near32(t0[i], best)) unsure = true;
+            if (sgn(i) != 0 && i != e && near32(t0[i], best)) unsure = true;
         if (e >= 0 && near32(best, r.tmin)) unsure = true;
         int ea;
         float te;
@@ -440,17 +444,17 @@ struct Walker {
             const int n = 1 << f.ldim(i);
             int v;
             if (i == ea) {
-                v = sg[i] > 0 ? 0 : n - 1;
+                v = sgn(i) > 0 ? 0 : n - 1;
             } else {
                 const float p = fmaf(te, r.d[i], r.o[i]);
                 const float fl = floorf(p);
                 v = (int)fminf(fmaxf(fl, -2.0f), 65536.0f);
-                if (sg[i] != 0) {
+                if (sgn(i) != 0) {
                     const float rq = rintf(p);
                     if (fabsf(p - rq) <= kGuard * (fabsf(te * r.d[i]) + fabsf(p))) {
                         VX_CNT(fp64, 1);
                         const double te64 = ea >= 0 ? t64(sel3(r.o, ea), sel3(r.d, ea),
-                                                          sel3(sg, ea) > 0 ? 0 : (1 << f.ldim(ea)))
+                                                          sgn(ea) > 0 ? 0 : (1 << f.ldim(ea)))
                                                     : (double)r.tmin;
                         v = start_coord64(r.o[i], r.d[i], te64);
                     }
@@ -481,8 +485,8 @@ struct Walker {
             for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
         }
         la = ea;                                                        // axis of the last crossing
-        lp = ea >= 0 ? (sel3(sg, ea) > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
         tcur = te;
+        lp = ea >= 0 ? (sgn(ea) > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
         fresh = true;  // no step taken yet
         // Every crossing this walk compares lies in [min(te, tx), max(te, tx)]
         // (crossings past the exit end it), and the FP32 error of one is at
@@ -503,7 +507,7 @@ struct Walker {
     // leaves the node.  Returns true once the ray is finished (out holds the
     // miss).
     __device__ __forceinline__ bool advance(const F& f, const Img im, HitRec& out) {
-        if (sg[0] == 0 && sg[1] == 0 && sg[2] == 0) {
+        if (r.d[0] == 0.0f && r.d[1] == 0.0f && r.d[2] == 0.0f) {
             out = miss_rec(ST_MISS);
             return true;
         }
@@ -512,8 +516,8 @@ struct Walker {
         float tn[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            pl[i] = (c[i] + (sg[i] > 0 ? 1 : 0)) << ls(f);
-            tn[i] = sg[i] != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
+            pl[i] = (c[i] + (sgn(i) > 0 ? 1 : 0)) << ls(f);
+            tn[i] = sgn(i) != 0 ? ((float)pl[i] - r.o[i]) * inv[i] : __int_as_float(0x7f800000);
         }
         int a = tn[1] < tn[0] ? 1 : 0;
         float tm = fminf(tn[0], tn[1]);
@@ -528,7 +532,7 @@ struct Walker {
         }
         // A step through the grid's boundary ends the walk whatever the exit
         // comparison says; only an exit on another axis or at tmax can tie.
-        const int pla = sel3(pl, a), sga = sel3(sg, a);
+        const int pla = sel3(pl, a), sga = sgn(a);
         bool out_now = pla == (sga > 0 ? (1 << f.ldim(a)) : 0);
         if (!out_now) {
             if (near(tm, tx)) {
@@ -639,7 +643,7 @@ struct Walker {
                 out.t = tcur;
                 out.rgba = term;
                 out.x = c[0]; out.y = c[1]; out.z = c[2];
-                out.face = la >= 0 ? 1 + 2 * la + (sel3(sg, la) < 0 ? 1 : 0) : 0;
+                out.face = la >= 0 ? 1 + 2 * la + (sgn(la) < 0 ? 1 : 0) : 0;
                 out.status = ST_HIT;
                 return true;
             }
@@ -661,8 +665,8 @@ struct Walker {
                 if (fresh) { c[i] = v0[i] >> sn; continue; }
                 const int base = c[i] << bn;
                 const int topc = base + (1 << bn) - 1;
-                if (i == la) { c[i] = sg[i] > 0 ? base : topc; continue; }
-                if (sg[i] == 0) { c[i] = v0[i] >> sn; continue; }
+                if (i == la) { c[i] = sgn(i) > 0 ? base : topc; continue; }
+                if (sgn(i) == 0) { c[i] = v0[i] >> sn; continue; }
                 const float p = fmaf(tcur, r.d[i], r.o[i]);
                 const float q = p * scale;
                 int cn = (int)fminf(fmaxf(floorf(q), (float)base), (float)topc);
@@ -671,10 +675,10 @@ struct Walker {
                     VX_CNT(fp64, 1);
                     const int B = (int)rq;
                     const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, sel3(r.o, la), sel3(r.d, la), lp, la);
-                    cn = sg[i] > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
+                    cn = sgn(i) > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
                 }
                 const int vs = v0[i] >> sn;
-                c[i] = sg[i] > 0 ? max(cn, vs) : min(cn, vs);
+                c[i] = sgn(i) > 0 ? max(cn, vs) : min(cn, vs);
             }
             return false;
         }
