@@ -231,9 +231,10 @@ static __device__ __noinline__ int argmin64(float o0, float o1, float o2, float 
 }
 
 // Is the crossing time tc (FP64) at or after the exit?
-static __device__ __noinline__ bool exits64(float o0, float o1, float o2, float d0, float d1, float d2, float tmin,
-                                            float tmax, int l0, int l1, int l2, float oa, float da, int plane) {
-    const Root64 R = root64(o0, o1, o2, d0, d1, d2, tmin, tmax, l0, l1, l2);
+// (The exit does not depend on tmin, so the walk need not keep it.)
+static __device__ __noinline__ bool exits64(float o0, float o1, float o2, float d0, float d1, float d2, float tmax,
+                                            int l0, int l1, int l2, float oa, float da, int plane) {
+    const Root64 R = root64(o0, o1, o2, d0, d1, d2, 0.0f, tmax, l0, l1, l2);
     return !(t64(oa, da, plane) < R.tx);
 }
 
@@ -537,7 +538,7 @@ struct Walker {
         if (!out_now) {
             if (near(tm, tx)) {
                 VX_CNT(fp64, 1);
-                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmin, r.tmax, f.ldim(0), f.ldim(1),
+                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmax, f.ldim(0), f.ldim(1),
                                   f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
             } else {
                 out_now = !(tm < tx);
