@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_trace_noalloc(DynF f, const Img pool,
                                                        int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint2 stack[DynF::kMaxJ];
+    uint2 stack[DynF::kMaxJ + 2];  // node stack + start voxel
     Walker<false, DynF> w;
     w.S = stack;
     bool live = false;

@@ -306,12 +306,12 @@ struct Walker {
     float gabs;  // guard band: 2^-20 of the largest |t| this walk compares
     float gpos;  // guard band for positions o + t d inside the grid
     // (direction sign per axis, -1 / 0 / 1: sgn(), from the ray)
-    int v0[3], c[3];
+    int c[3];  // cell at node level j (the start voxel is kept in the stack array)
     int j, la, lp, budget;
     int skip;  // DF level: cells the walk may still enter without a look-up
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
-    uint2* S;         // this thread's node stack, F::kMaxJ entries (owned by the caller)
+    uint2* S;         // owned by the caller: F::kMaxJ node-stack entries, then 2 holding the start voxel
     uint32_t lim;     // words in the image (checked by the instrumented walker)
     Cnt cnt;
 
@@ -440,6 +440,7 @@ struct Walker {
         }
 
         // ---- start voxel ----
+        int v0l[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             const int n = 1 << f.ldim(i);
@@ -461,8 +462,12 @@ struct Walker {
                     }
                 }
             }
-            v0[i] = min(max(v, 0), n - 1);
+            v0l[i] = min(max(v, 0), n - 1);
         }
+        // the start voxel is read only by descents before the first step:
+        // it lives in the stack array's two extra entries, not in registers
+        S[F::kMaxJ] = make_uint2((uint32_t)v0l[0], (uint32_t)v0l[1]);
+        S[F::kMaxJ + 1] = make_uint2((uint32_t)v0l[2], 0u);
 
         // ---- root node ----
         const uint32_t root = rd(pool, 0);
@@ -483,7 +488,7 @@ struct Walker {
         {
             const int s0 = f.s(0);
 #pragma unroll
-            for (int i = 0; i < 3; i++) c[i] = v0[i] >> s0;
+            for (int i = 0; i < 3; i++) c[i] = v0l[i] >> s0;
         }
         la = ea;                                                        // axis of the last crossing
         tcur = te;
@@ -661,13 +666,19 @@ struct Walker {
             Mc = Mn;
             const int sn = ls(f), bn = lb(f, 0);
             const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
+            if (fresh) {  // no step yet: the cell holding the start voxel
+                const uint2 a01 = S[F::kMaxJ], a2 = S[F::kMaxJ + 1];
+                c[0] = (int)a01.x >> sn;
+                c[1] = (int)a01.y >> sn;
+                c[2] = (int)a2.x >> sn;
+                return false;
+            }
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                if (fresh) { c[i] = v0[i] >> sn; continue; }
                 const int base = c[i] << bn;
                 const int topc = base + (1 << bn) - 1;
                 if (i == la) { c[i] = sgn(i) > 0 ? base : topc; continue; }
-                if (sgn(i) == 0) { c[i] = v0[i] >> sn; continue; }
+                if (sgn(i) == 0) { c[i] = (int)floorf(r.o[i]) >> sn; continue; }  // o inside the grid on that axis
                 const float p = fmaf(tcur, r.d[i], r.o[i]);
                 const float q = p * scale;
                 int cn = (int)fminf(fmaxf(floorf(q), (float)base), (float)topc);
@@ -677,9 +688,14 @@ struct Walker {
                     const int B = (int)rq;
                     const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, sel3(r.o, la), sel3(r.d, la), lp, la);
                     cn = sgn(i) > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
+                    // a ray that started on plane B took the start voxel's
+                    // convention; a crossing at that same instant must not undo it
+                    // (away from the band the cell is past the start anyway)
+                    const uint2 sv = i == 2 ? S[F::kMaxJ + 1] : S[F::kMaxJ];
+                    const int vs = (int)(i == 1 ? sv.y : sv.x) >> sn;
+                    cn = sgn(i) > 0 ? max(cn, vs) : min(cn, vs);
                 }
-                const int vs = v0[i] >> sn;
-                c[i] = sgn(i) > 0 ? max(cn, vs) : min(cn, vs);
+                c[i] = cn;
             }
             return false;
         }
@@ -692,7 +708,7 @@ struct Walker {
 
 template <bool COUNT, class F, bool RESTART = false>
 __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt) {
-    uint2 stack[F::kMaxJ];
+    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
     Walker<COUNT, F, RESTART> w;
     w.S = stack;
     HitRec h;
@@ -820,7 +836,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
                                                            unsigned long long* next, int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint2 stack[F::kMaxJ];
+    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
     Walker<false, F> w;
     w.S = stack;
     bool live = false;
@@ -886,7 +902,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
             for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) vx_top_smem[i] = ldw(pool.w, root + i);
         __syncthreads();
     }
-    uint2 stack[F::kMaxJ];
+    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
     Walker<false, F, RS, TS> w;
     w.S = stack;
     bool live = false;
@@ -946,7 +962,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t n = desc.start[desc.count];
-    uint2 stack[F::kMaxJ];
+    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
     Walker<false, F> w;
     w.S = stack;
     bool live = false;
