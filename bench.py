@@ -97,6 +97,33 @@ def ncu_counters(kernel_key: str):
 ISSUE_PEAK_GINST_S = 148 * 4 * 2.032
 
 
+def pcie_both_ways_gbs(nbytes: int = 256 << 20, reps: int = 5) -> float:
+    """Host<->device copy rate (GB/s, both directions summed) with one
+    pinned-host upload and one download in flight at once on two streams."""
+    import torch
+    h_up = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_dn = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_up = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_dn = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def both():
+        with torch.cuda.stream(s_up):
+            d_up.copy_(h_up, non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            h_dn.copy_(d_dn, non_blocking=True)
+
+    both()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        both()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    del h_up, h_dn, d_up, d_dn
+    return 2 * nbytes / dt / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -384,13 +411,20 @@ def run_gpu(args):
 
         outs = [(pinned_hits(n_prim), pinned_hits(N_INC)) for _ in vols]
         # one host thread per volume: the calls block, and each volume has its
-        # own staging buffers and streams, so one volume's downloads overlap the
-        # other's uploads (the library releases the GIL during its calls)
+        # own staging buffers and streams (the library releases the GIL during
+        # its calls).  A render only downloads and a trace mostly uploads, so
+        # alternate volumes take them in opposite orders: one volume's render
+        # downloads while the other's trace uploads, and both PCIe directions
+        # stay busy for the whole step.
         pool = ThreadPoolExecutor(max_workers=len(vols))
 
         def one_volume(k):
-            vols[k].render_host(cam, out=outs[k][0])
-            vols[k].trace_host(pin_rays, out=outs[k][1])
+            if k % 2 == 0:
+                vols[k].render_host(cam, out=outs[k][0])
+                vols[k].trace_host(pin_rays, out=outs[k][1])
+            else:
+                vols[k].trace_host(pin_rays, out=outs[k][1])
+                vols[k].render_host(cam, out=outs[k][0])
 
         def e2e_step():
             for f in [pool.submit(one_volume, k) for k in range(len(vols))]:
@@ -410,10 +444,21 @@ def run_gpu(args):
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": round(world * rays_per_step * args.steps / dt / 1e6, 3), "unit": UNIT,
-               "h2d_bytes_per_step": len(FORMATS) * N_INC * 32,
-               "d2h_bytes_per_step": len(FORMATS) * (n_prim + N_INC) * 16,
-               "api": "vx_render_host + vx_trace_host, pinned host buffers, one host thread per volume"}
+        h2d = len(FORMATS) * N_INC * 32
+        d2h = len(FORMATS) * (n_prim + N_INC) * 16
+        # The bound of this path is PCIe: the step's bytes over the copy rate
+        # with both directions busy at once, measured here with plain copies.
+        pcie = pcie_both_ways_gbs()
+        bound = rays_per_step / ((h2d + d2h) / (pcie * 1e9)) / 1e6
+        e2e_value = world * rays_per_step * args.steps / dt / 1e6
+        e2e = {"value": round(e2e_value, 3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "pcie": {"bound": "pcie", "peak_gbs_both_ways": round(pcie, 1),
+                        "bound_mrays_s": round(bound, 1), "frac": round(e2e_value / world / bound, 4),
+                        "peak_source": "256 MiB pinned-host copies, one up and one down at once, timed here"},
+               "api": "vx_render_host + vx_trace_host, pinned host buffers, one host thread per volume "
+                      "(alternate volumes render first / trace first)"}
         pool.shutdown()
 
     # --- CPU baseline: the oracle on a bounded sample ---
