@@ -271,12 +271,15 @@ def run_gpu(args):
     for k, v in enumerate(vols):
         for name, rays in (("render", prim_rays), ("trace", inc)):
             c = torch.zeros(4, dtype=torch.int64, device="cuda")
+            sect = v.alloc_sectors()
             tmp = vx.alloc_hits(rays.shape[0])
-            v.trace_counted(rays, tmp, c)
+            v.trace_counted(rays, tmp, c, sectors=sect)
             torch.cuda.synchronize()
             b, it, d, _ = (int(x) for x in c.cpu())
             n = rays.shape[0]
-            counts[(k, name)] = {"node_bytes_per_ray": b / n, "iters_per_ray": it / n, "fp64_per_ray": d / n}
+            counts[(k, name)] = {"node_bytes_per_ray": b / n, "iters_per_ray": it / n, "fp64_per_ray": d / n,
+                                 "footprint_bytes": vx.Volume.footprint_bytes(sect)}
+            del sect
     del prim_rays
 
     def step(evs=None, mode=mode):
@@ -365,6 +368,7 @@ def run_gpu(args):
             "node_bytes_per_ray_incoherent": round(counts[(k, "trace")]["node_bytes_per_ray"], 2),
             "iters_per_ray_incoherent": round(counts[(k, "trace")]["iters_per_ray"], 2),
             "fp64_decisions_per_ray_incoherent": round(counts[(k, "trace")]["fp64_per_ray"], 5),
+            "format_footprint_bytes_incoherent": counts[(k, "trace")]["footprint_bytes"],
             "specialized_kernel": st["specialized"],
             "tuned_trace_opts": tuned[k] if tuned else None,
         })
@@ -384,8 +388,14 @@ def run_gpu(args):
     # kernel does not count)
     kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}:{kname}"
     traffic, insts = ncu_counters(kernel_key)
+    # compulsory bytes: the distinct 32-byte sectors of the format the launch
+    # reads (sector bitmap of the instrumented kernel) plus the ray/hit I/O,
+    # the least DRAM traffic a launch with cold caches can have
+    compulsory = counts[dom]["footprint_bytes"] + n_rays * io
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "dram_frac": round(traffic / (avg_ms / 1e3) / 1e9 / peak, 4) if traffic else None,
+                "compulsory_bytes_per_launch": int(compulsory),
                 "kernel": f"{kname} {FORMATS[k]}",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
@@ -630,10 +640,12 @@ def run_formats512(args):
         ms_r = _timed(torch, lambda: v.render(cam, hp), args.steps, args.warmup)
         ms_t = _timed(torch, lambda: v.trace(inc, hi), args.steps, args.warmup)
         c = torch.zeros(4, dtype=torch.int64, device="cuda")
-        v.trace_counted(inc, hi, c)
+        sect = v.alloc_sectors()
+        v.trace_counted(inc, hi, c, sectors=sect)
         torch.cuda.synchronize()
         b, it, _, _ = (int(x) for x in c.cpu())
         per.append({"format": spec, "table2": LABEL.get(spec), "build_s": round(build_s, 2),
+                    "format_footprint_bytes_incoherent": vx.Volume.footprint_bytes(sect),
                     "device_bytes": st["device_bytes"], "canonical_bytes": st["canonical_bytes"],
                     "bytes_per_voxel": round(st["device_bytes"] / N_VOL ** 3, 5),
                     "specialized_kernel": st["specialized"],

@@ -275,9 +275,16 @@ int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hi
  * algorithmic traffic of the method.  This kernel checks every read of the
  * volume against its size: a refused read counts in [3] and the ray's hit
  * reports VX_STATUS_ERROR, so it is the one trace that may read a volume
- * loaded without validation (vx_load). */
+ * loaded without validation (vx_load).
+ *   sectors  NULL, or a caller-zeroed device array of
+ *            ceil(device_bytes / 1024) uint32 words (4-byte aligned; see
+ *            vx_stats): bit (s & 31) of word s >> 5 is set when the traversal
+ *            read any word of the s-th 32-byte sector of the device image.
+ *            Its popcount x 32 B is the format's footprint in the launch, the
+ *            bytes a cold cache must fetch from DRAM at least.  Bits are only
+ *            ever set (atomic OR), so calls may accumulate into one array. */
 int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
-                     const vx_trace_opts* opts, void* stream, unsigned long long* counters);
+                     const vx_trace_opts* opts, void* stream, unsigned long long* counters, uint32_t* sectors);
 
 /* Several ray sets, possibly through different volumes (all on one device),
  * in one call: the sets are grouped by format, each group (up to 64 sets) is

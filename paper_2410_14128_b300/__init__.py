@@ -93,7 +93,8 @@ _SIGS = {
     "vx_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_trace_counted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
-                                        ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p]),
+                                        ctypes.c_int32, ctypes.POINTER(_TraceOpts), ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "vx_trace_batch": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
                                       ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -326,15 +327,32 @@ class Volume:
                               layout, ctypes.byref(o), _stream_handle(stream)))
         return hits
 
-    def trace_counted(self, rays, hits, counters, layout: int = HIT_FULL, stream=None, **opts):
+    def trace_counted(self, rays, hits, counters, layout: int = HIT_FULL, stream=None, sectors=None, **opts):
         """As trace(), adding [bytes read, iterations, FP64 decisions, reads
-        refused] into `counters` (CUDA int64 tensor of 4, caller-zeroed)."""
+        refused] into `counters` (CUDA int64 tensor of 4, caller-zeroed) and,
+        if `sectors` is given (CUDA int32 tensor from alloc_sectors(),
+        caller-zeroed), setting one bit per 32-byte sector of the device image
+        the traversal read."""
         n = rays.shape[0]
         o = _opts(**opts)
+        sp = ctypes.c_void_p(sectors.data_ptr()) if sectors is not None else None
         _check(lib().vx_trace_counted(self._h, ctypes.c_void_p(rays.data_ptr()), n, ctypes.c_void_p(hits.data_ptr()),
                                       layout, ctypes.byref(o), _stream_handle(stream),
-                                      ctypes.c_void_p(counters.data_ptr())))
+                                      ctypes.c_void_p(counters.data_ptr()), sp))
         return hits
+
+    def alloc_sectors(self):
+        """Zeroed CUDA int32 tensor sized for trace_counted(sectors=...): one
+        bit per 32-byte sector of the device image."""
+        import torch
+        words = (self.stats()["device_bytes"] + 1023) // 1024
+        return torch.zeros(max(1, words), dtype=torch.int32, device="cuda")
+
+    @staticmethod
+    def footprint_bytes(sectors) -> int:
+        """Bytes of the device image in the sectors marked by trace_counted."""
+        bits = np.unpackbits(sectors.cpu().numpy().view(np.uint8))
+        return 32 * int(bits.sum())
 
     def autotune(self, sample_rays, stream=None) -> dict:
         """Times trace options on a device sample of rays; vx_trace with the

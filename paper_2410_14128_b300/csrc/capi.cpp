@@ -343,7 +343,8 @@ extern "C" int vx_trace(vx_volume v, const vx_ray* rays, uint64_t n, void* hits,
 }
 
 extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, int32_t hit_layout,
-                                const vx_trace_opts* opts, void* stream, unsigned long long* counters) {
+                                const vx_trace_opts* opts, void* stream, unsigned long long* counters,
+                                uint32_t* sectors) {
     clear_error();
     int rc = check_trace_args(v, rays, n, hits, hit_layout, true);
     if (!rc) rc = check_opts(opts);
@@ -351,9 +352,10 @@ extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, voi
     if ((rc = check_ptrs(rays, hits, hit_layout))) return rc;
     if (!rays) return fail(VX_EINVAL, "rays is NULL");
     if (!counters || !aligned(counters, 8)) return fail(VX_EINVAL, "counters must be an 8-byte aligned device array");
+    if (sectors && !aligned(sectors, 4)) return fail(VX_EINVAL, "sectors must be a 4-byte aligned device array");
     DeviceScope ds(v->v.device);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
-    return launch_trace_count(v->v, rays, n, hits, hit_layout, opts, stream, counters);
+    return launch_trace_count(v->v, rays, n, hits, hit_layout, opts, stream, counters, sectors);
 }
 
 extern "C" int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layout,

@@ -181,11 +181,11 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
 }
 
 int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout,
-                       const vx_trace_opts* o, void* stream, unsigned long long* counters) {
+                       const vx_trace_opts* o, void* stream, unsigned long long* counters, uint32_t* sectors) {
     const int block = pick_block(o);
     const int restart = o ? o->restart : 0;
     int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), n, hits, layout,
-                                   block, restart, (cudaStream_t)stream, counters);
+                                   block, restart, (cudaStream_t)stream, counters, sectors);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
 }

@@ -313,15 +313,20 @@ struct Walker {
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
     uint2* S;         // owned by the caller: F::kMaxJ node-stack entries, then 2 holding the start voxel
     uint32_t lim;     // words in the image (checked by the instrumented walker)
+    uint32_t* sect;   // instrumented walker: one bit per 32-byte sector of the image it read, or null
     Cnt cnt;
 
     // A word of the image.  The instrumented walker (COUNT) checks every
     // index against the image size and refuses reads outside it (counted; the
-    // ray then reports ST_ERROR), so it can walk a buffer nobody validated.
+    // ray then reports ST_ERROR), so it can walk a buffer nobody validated;
+    // it also marks the 32-byte sector (8 words) each accepted read falls in.
     __device__ __forceinline__ uint32_t rd(const uint32_t* __restrict__ pool, uint32_t i) {
-        if (COUNT && i >= lim) {
-            cnt.refused++;
-            return 0u;
+        if (COUNT) {
+            if (i >= lim) {
+                cnt.refused++;
+                return 0u;
+            }
+            if (sect) atomicOr(sect + (i >> 8), 1u << ((i >> 3) & 31u));
         }
         return ldw(pool, i);
     }
@@ -707,10 +712,12 @@ struct Walker {
 #undef VX_CNT
 
 template <bool COUNT, class F, bool RESTART = false>
-__device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt) {
+__device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt,
+                                            uint32_t* sect = nullptr) {
     uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
     Walker<COUNT, F, RESTART> w;
     w.S = stack;
+    w.sect = sect;
     HitRec h;
     if (!w.start(f, pool, r, h))
         while (!w.step(f, pool, h)) {
@@ -805,12 +812,13 @@ __global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __res
 template <class F, int LAYOUT, bool RS = false>
 __global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
                                                      const float4* __restrict__ rays, uint64_t n,
-                                                     void* __restrict__ hits, unsigned long long* counters) {
+                                                     void* __restrict__ hits, unsigned long long* counters,
+                                                     uint32_t* sectors) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     Cnt cnt;
     if (i < n) {
         const RayIn r = load_ray(rays, i);
-        const HitRec h = trace_ray<true, F, RS>(f, pool, r, cnt);
+        const HitRec h = trace_ray<true, F, RS>(f, pool, r, cnt, sectors);
         store_hit<LAYOUT>(f, hits, i, h);
     }
     unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64, rf = cnt.refused;
@@ -1039,7 +1047,8 @@ struct KernelSet {
     int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
-                       int layout, int block, int restart, cudaStream_t st, unsigned long long* counters);
+                       int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
+                       uint32_t* sectors);
     int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
                             int restart, int smem_top, cudaStream_t st, unsigned long long* next);
@@ -1067,18 +1076,19 @@ struct Launch {
         return (int)cudaGetLastError();
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
-                           int layout, int block, int restart, cudaStream_t st, unsigned long long* counters) {
+                           int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
+                           uint32_t* sectors) {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
         if (layout == 0 && !restart)
-            k_trace_count<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
         else if (layout == 0)
-            k_trace_count<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
         else if (!restart)
-            k_trace_count<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
         else
-            k_trace_count<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters);
+            k_trace_count<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
         return (int)cudaGetLastError();
     }
     // Words of a Raw / DF top level that fits the shared-memory staging, else 0.

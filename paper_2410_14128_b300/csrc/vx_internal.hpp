@@ -157,7 +157,7 @@ const KernelSet* generic_kernels();
 int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
                  void* stream);
 int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout,
-                       const vx_trace_opts* o, void* stream, unsigned long long* counters);
+                       const vx_trace_opts* o, void* stream, unsigned long long* counters, uint32_t* sectors);
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);

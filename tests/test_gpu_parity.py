@@ -590,3 +590,81 @@ def test_checked_trace_refuses_reads_outside_a_corrupt_buffer():
         assert c2[3] > 0
         assert set(np.unique(st).tolist()) <= {vx.STATUS_MISS, vx.STATUS_HIT, vx.STATUS_ERROR}
         assert (st == vx.STATUS_ERROR).sum() > 0
+
+
+# ---------------------------------------------------------------------------
+# Format footprint: the sector bitmap of the instrumented kernel
+# ---------------------------------------------------------------------------
+def _sectors(vol, rays, sect=None, **opts):
+    r = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
+    c = torch.zeros(4, dtype=torch.int64, device="cuda")
+    s = vol.alloc_sectors() if sect is None else sect
+    h = vx.alloc_hits(len(rays))
+    vol.trace_counted(r, h, c, sectors=s, **opts)
+    torch.cuda.synchronize()
+    bits = np.unpackbits(s.cpu().numpy().view(np.uint8), bitorder="little")
+    return set(np.nonzero(bits)[0].tolist()), [int(x) for x in c.cpu()], s
+
+
+def test_footprint_of_axis_rays_through_one_raw_level_is_exact():
+    # R(3,3,3): word 0 holds the root pointer, cell (x, y, z) is word
+    # root + x + 8 y + 64 z; a ray along an axis from outside the grid reads
+    # word 0 and the cells it walks, up to its first occupied cell
+    g = synth.random_grid(141, (8, 8, 8), 0.15, colors=3)
+    vol = vx.Volume("R(3,3,3)", g)
+    root = int(vol.canonical()[0])
+    rng = np.random.default_rng(142)
+    rays, want = [], {0}
+    for _ in range(300):
+        ax = int(rng.integers(0, 3))
+        sgn = 1 if rng.random() < 0.5 else -1
+        a, b = rng.integers(0, 8, size=2)
+        o = [0.0, 0.0, 0.0]
+        d = [0.0, 0.0, 0.0]
+        others = [i for i in range(3) if i != ax]
+        o[others[0]], o[others[1]] = a + 0.5, b + 0.5
+        o[ax] = -1.5 if sgn > 0 else 9.5
+        d[ax] = float(sgn)
+        rays.append(o + [0.0] + d + [np.inf])
+        for k in (range(8) if sgn > 0 else range(7, -1, -1)):
+            v = [0, 0, 0]
+            v[ax], v[others[0]], v[others[1]] = k, int(a), int(b)
+            want.add((root + v[0] + 8 * v[1] + 64 * v[2]) >> 3)
+            if g[v[2], v[1], v[0]] != 0:
+                break
+    rays = np.array(rays, np.float32)
+    got, c, _ = _sectors(vol, rays)
+    assert c[3] == 0
+    assert got == want
+
+
+@pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "D(3,3,3,6) G(4)", "G(7)"])
+def test_footprint_properties(spec):
+    g = synth.terrain_volume(143, 128)
+    vol = vx.Volume(spec, g)
+    words = vol.stats()["device_bytes"] // 4
+    a = synth.incoherent_rays(144, 128, 30001)
+    b = synth.box_rays(145, 128, 40, 20000)
+    sa, ca, _ = _sectors(vol, a)
+    sb, _, _ = _sectors(vol, b)
+    sab, cab, _ = _sectors(vol, np.concatenate([a, b]))
+    assert sab == sa | sb                      # the union of the two sets
+    assert max(sab) < (words + 7) // 8         # only sectors of the image
+    assert 0 in sab                            # the root pointer
+    assert len(sab) <= cab[0] // 4             # at most one new sector per word read
+    # calls accumulate into one array; tracing the same rays again adds nothing
+    acc, _, s = _sectors(vol, a)
+    acc2, _, _ = _sectors(vol, b, sect=s)
+    assert acc2 == sab
+    acc3, _, _ = _sectors(vol, a, sect=s)
+    assert acc3 == sab
+    # the restarting traversal re-reads nodes it has already read
+    sr, cr, _ = _sectors(vol, a, restart=True)
+    assert sr == sa and cr[0] >= ca[0]
+    assert vx.Volume.footprint_bytes(s) == 32 * len(sab)
+    # rays that miss the root box read nothing
+    miss = a.copy()
+    miss[:, 0:3] = (-10.0, -10.0, -10.0)
+    miss[:, 4:7] = (-1.0, 0.0, 0.0)
+    sm, cm, _ = _sectors(vol, miss)
+    assert sm == set() and cm[0] == 0
