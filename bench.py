@@ -193,7 +193,7 @@ def oracle_rate(grid, cam, inc, budget_s: float, threads: int | None = None):
     rng = np.random.default_rng(5)
     pi = rng.permutation(len(prim))
     ii = rng.permutation(len(inc))
-    chunk = max(20000, 2048 * (os.cpu_count() or 1))
+    chunk = max(20000, 2048 * (threads or os.cpu_count() or 1))
     done, t_used, used_threads, k = 0, 0.0, 1, 0
     while t_used < budget_s and (k + 1) * chunk <= min(len(prim), len(inc)):
         sample = np.concatenate([prim[pi[k * chunk:(k + 1) * chunk]], inc[ii[k * chunk:(k + 1) * chunk]]])
@@ -282,18 +282,33 @@ def run_gpu(args):
             del sect
     del prim_rays
 
+    # The step's four launches are independent: the renders go on the main
+    # stream and the traces on a second one, so a launch's tail (its last
+    # warps, while most SMs have run out of rays) overlaps the next launch of
+    # the other stream.  Both start after the L2 flush; the main stream waits
+    # for the traces before the step ends.
+    side = torch.cuda.Stream()
+
     def step(evs=None, mode=mode):
         flush.zero_()
+        main = torch.cuda.current_stream()
+        flushed = torch.cuda.Event()
+        flushed.record(main)
+        side.wait_event(flushed)
         for k, v in enumerate(vols):
-            if evs is not None:
-                evs[(k, "render")][0].record()
-            v.render(cam, hits_p[k])
-            if evs is not None:
-                evs[(k, "render")][1].record()
-                evs[(k, "trace")][0].record()
-            v.trace(inc, hits_i[k], mode=mode)
-            if evs is not None:
-                evs[(k, "trace")][1].record()
+            for name, st in (("render", main), ("trace", side)):
+                with torch.cuda.stream(st):
+                    if evs is not None:
+                        evs[(k, name)][0].record(st)
+                    if name == "render":
+                        v.render(cam, hits_p[k])
+                    else:
+                        v.trace(inc, hits_i[k], mode=mode)
+                    if evs is not None:
+                        evs[(k, name)][1].record(st)
+        traced = torch.cuda.Event()
+        traced.record(side)
+        main.wait_event(traced)
 
     # the plain one-thread-per-ray kernel on the same step, for comparison
     plain_ms = None
@@ -348,6 +363,26 @@ def run_gpu(args):
 
     # --- per-format results and the roofline of the dominant kernel ---
     peak, peak_kind = load_peaks()
+    # Each launch alone (after the timed region; L2 flushed before each), for
+    # the kernels' own speed: inside the step they share the GPU with the
+    # other stream's launches.
+    alone = {}
+    for key in counts:
+        k, name = key
+        ts = []
+        for r in range(12):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if name == "render":
+                vols[k].render(cam, hits_p[k])
+            else:
+                vols[k].trace(inc, hits_i[k], mode=mode)
+            b.record()
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        alone[key] = float(np.mean([a.elapsed_time(b) for a, b in ts[2:]]))
+
     per_format = []
     tot = {}
     for k, spec in enumerate(FORMATS):
@@ -361,6 +396,8 @@ def run_gpu(args):
             "mrays_s_primary": round(n_prim / ms_r / 1e3, 2),
             "mrays_s_incoherent": round(N_INC / ms_t / 1e3, 2),
             "mrays_s": round((n_prim + N_INC) / (ms_r + ms_t) / 1e3, 2),
+            "mrays_s_primary_alone": round(n_prim / alone[(k, "render")] / 1e3, 2),
+            "mrays_s_incoherent_alone": round(N_INC / alone[(k, "trace")] / 1e3, 2),
             "device_bytes": st["device_bytes"],
             "bytes_per_voxel": round(st["device_bytes"] / N_VOL ** 3, 5),
             "bytes_per_occupied_voxel": round(st["device_bytes"] / max(1, st["occupied_voxels"]), 4),
@@ -398,6 +435,7 @@ def run_gpu(args):
                 "compulsory_bytes_per_launch": int(compulsory),
                 "kernel": f"{kname} {FORMATS[k]}",
                 "alg_bytes_per_launch": int(alg_bytes), "avg_launch_ms": round(avg_ms, 4),
+                "avg_launch_ms_alone": round(alone[dom], 4),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     # The traversal is a chain of dependent small reads that mostly hit in L1/L2,
     # so the unit that limits it is instruction issue: warp instructions per
@@ -475,9 +513,11 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, thr, n, t = oracle_rate(grid, cam, inc_np, budget_s=args.cpu_budget_s)
+        v1, _, n1, t1 = oracle_rate(grid, cam, inc_np, budget_s=min(5.0, args.cpu_budget_s), threads=1)
         cpu = {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{n} rays of the step (half pinhole, half incoherent), {t:.1f} s of FP64 oracle on "
-                         f"the uncompressed 512^3 grid; format-independent"}
+                         f"the uncompressed 512^3 grid; format-independent",
+               "single_core": {"value": round(v1, 4), "sample": f"{n1} rays, {t1:.1f} s on one thread"}}
 
     if rank == 0:
         line = {
@@ -488,6 +528,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"flushed before each step by a {FLUSH_BYTES >> 20} MiB write (inside the timed region)",
                        "hit_layout": "full 16 B",
+                       "streams": "renders on one stream, traces on a second, overlapping within the step",
                        "mode": {"auto": "auto (vx_trace options autotuned per format on the incoherent rays, outside the timed region)",
                                 "plain": "plain (one thread per ray)",
                                 "persistent": "persistent warps with ray refill"}[args.mode]},
