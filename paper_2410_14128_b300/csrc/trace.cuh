@@ -1023,16 +1023,28 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     }
 }
 
+constexpr uint32_t kTileW = 8, kTileH = 32 / kTileW;  // pixels of a warp's tile
+
 template <class F, int LAYOUT>
 __global__ void VX_PLAIN_BOUNDS k_render(F f, const Img pool, CamDev cam, uint64_t i0,
-                                                uint64_t n, void* __restrict__ hits) {
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const uint64_t i = i0 + k;
-    const RayIn r = pinhole_ray(cam, (uint32_t)(i % cam.W), (uint32_t)(i / cam.W));
+                                                uint64_t n, uint32_t y0, uint32_t tiles_w,
+                                                void* __restrict__ hits) {
+    // Each warp takes a tile of 8 x 4 pixels (tiles row by row from image row
+    // y0): neighbouring rays follow nearly the same path through the format,
+    // and a compact tile has fewer lanes on a silhouette than a 32-pixel run.
+    // Pixels outside the image or outside [i0, i0 + n) are skipped.
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t tile = t >> 5;
+    const uint32_t lane = (uint32_t)t & 31u;
+    const uint32_t px = (uint32_t)(tile % tiles_w) * kTileW + (lane % kTileW);
+    const uint64_t py = (uint64_t)y0 + (tile / tiles_w) * kTileH + (lane / kTileW);
+    if (px >= cam.W) return;
+    const uint64_t i = py * cam.W + px;
+    if (i < i0 || i - i0 >= n) return;
+    const RayIn r = pinhole_ray(cam, px, (uint32_t)py);
     Cnt cnt;
     const HitRec h = trace_ray<false>(f, pool, r, cnt);
-    store_hit<LAYOUT>(f, hits, k, h);
+    store_hit<LAYOUT>(f, hits, i - i0, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -1189,9 +1201,16 @@ struct Launch {
                       void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);
-        const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0) k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
-        else k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits);
+        // 8 x 4 pixel tiles over the image rows that hold pixels i0 .. i0 + n - 1
+        const uint64_t y0 = i0 / cam.W, y1 = (i0 + n - 1) / cam.W;
+        const uint64_t tiles_w = (cam.W + kTileW - 1) / kTileW, tile_rows = (y1 - y0 + kTileH) / kTileH;
+        const uint64_t threads = tiles_w * tile_rows * 32u;
+        const uint64_t grid = (threads + (uint64_t)block - 1) / (uint64_t)block;
+        if (grid > 0x7FFFFFFFull) return (int)cudaErrorInvalidConfiguration;
+        if (layout == 0)
+            k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
+        else
+            k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
         return (int)cudaGetLastError();
     }
 };

@@ -218,6 +218,23 @@ def test_render_equals_trace_of_raygen():
     assert np.array_equal(hc["t"], full["t"])
 
 
+@pytest.mark.parametrize("W,H", [(7, 5), (1001, 767), (33, 4097)])
+def test_render_ragged_tiles_and_chunks(W, H):
+    # image sides that are not multiples of the 8 x 4 warp tile, and (for
+    # the host variant) chunks of 2^18 pixels that start in the middle of a row
+    g = synth.terrain_volume(43, 128)
+    vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
+    cam = synth.camera(44, 128, W, H, mode="above")
+    rays = vx.raygen_pinhole(cam)
+    h1 = vx.alloc_hits(rays.shape[0])
+    vol.trace(rays, h1)
+    h2 = vx.alloc_hits(rays.shape[0])
+    vol.render(cam, h2, block=64)
+    torch.cuda.synchronize()
+    assert torch.equal(h1, h2)
+    assert np.array_equal(vol.render_host(cam), vx.hits_to_numpy(h1))
+
+
 def test_trace_host_multi_chunk():
     g = synth.random_grid(51, (64, 64, 64), 0.03)
     vol = vx.Volume("R(2,2,2) G(4)", g)
