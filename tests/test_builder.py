@@ -40,6 +40,29 @@ def test_library_exports_every_header_function():
     assert vx.lib().vx_version() >= 10000
 
 
+def test_binding_argument_counts_match_header():
+    # every C declaration and its ctypes signature take the same number of
+    # arguments (a parameter added on one side only would shift the rest)
+    with open(os.path.join(ROOT, "include", "vx.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    decls = re.findall(r"^(?:int|const char\*)\s+(vx_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.M | re.S)
+    assert {n for n, _ in decls} == set(header_functions())
+    for name, params in decls:
+        p = params.strip()
+        count = 0 if p in ("", "void") else p.count(",") + 1
+        assert len(vx._SIGS[name][1]) == count, name
+
+
+def test_footprint_bytes_counts_marked_sectors():
+    torch = pytest.importorskip("torch")
+    words = np.zeros(5, np.uint32)
+    words[0] = 0b1011            # sectors 0, 1, 3
+    words[3] = 1 << 31           # sector 127
+    words[4] = 0xFFFFFFFF        # sectors 128..159
+    t = torch.from_numpy(words.view(np.int32))
+    assert vx.Volume.footprint_bytes(t) == 32 * (3 + 1 + 32)
+
+
 # ---------------------------------------------------------------------------
 # Spec parser
 # ---------------------------------------------------------------------------
