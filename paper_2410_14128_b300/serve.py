@@ -17,6 +17,11 @@ clock).  Each loop iteration
 3. polls the events of earlier epochs and completes finished requests,
    releasing their budget.
 
+A request that is malformed (unknown volume, bad camera, rays not an (n, 8)
+float32 array) is refused when submitted, and one that the library rejects
+when launched (e.g. a camera with an invalid field of view) is refused then,
+with its memory released: a bad request never stops the others.
+
 Epochs on different streams overlap on the GPU, so requests that arrive
 while others run are admitted as soon as memory and slots free up (continuous
 batching), not after the whole queue drains.  Latency = completion - arrival.
@@ -30,7 +35,7 @@ from collections import deque
 
 import numpy as np
 
-from . import HIT_FULL, alloc_hits, hit_dtype, trace_batch
+from . import HIT_FULL, VxError, alloc_hits, hit_dtype, trace_batch
 
 HIT_BYTES = {0: 16, 1: 8}
 
@@ -147,7 +152,43 @@ class Server:
         return ray_bytes + HIT_BYTES[self.layout] * req.n
 
     def submit(self, req: Request):
+        why = self.invalid(req)
+        if why:
+            now = self.now()
+            self.results[req.id] = Result(req.id, None, req.arrival, now, now, refused=f"invalid request: {why}")
+            return
         self.pending.append(req)
+
+    def invalid(self, req: Request) -> str | None:
+        """Why `req` cannot be served (None if it can): checked on the host
+        before it takes any memory."""
+        if req.volume not in self.volumes:
+            return f"unknown volume {req.volume!r}"
+        if (req.camera is None) == (req.rays is None):
+            return "give exactly one of camera and rays"
+        if req.camera is not None:
+            try:
+                w, h = int(req.camera["width"]), int(req.camera["height"])
+                for key in ("eye", "look", "up"):
+                    if len(req.camera[key]) != 3:
+                        return f"camera {key} needs 3 components"
+                float(req.camera["vfov_deg"])
+            except (KeyError, TypeError, ValueError) as e:
+                return f"bad camera ({e!r})"
+            if w <= 0 or h <= 0:
+                return "camera image is empty"
+            return None
+        r = req.rays
+        if not isinstance(r, np.ndarray) or r.dtype != np.float32 or r.ndim != 2 or r.shape[1] != 8:
+            return "rays must be an (n, 8) float32 array"
+        if not r.flags.c_contiguous:
+            return "rays must be C-contiguous"
+        return None
+
+    def _refuse(self, req, now, need, slot, why):
+        self.arena.release(*slot)
+        self.used -= need
+        self.results[req.id] = Result(req.id, None, req.arrival, now, self.now(), refused=why)
 
     # -- one iteration --------------------------------------------------------
     def step(self) -> int:
@@ -208,7 +249,11 @@ class Server:
             k, stream = self._stream()
             with torch.cuda.stream(stream):
                 hits = alloc_hits(req.n, self.layout)
-                vol.render(req.camera, hits, self.layout, stream=stream)
+                try:
+                    vol.render(req.camera, hits, self.layout, stream=stream)
+                except VxError as e:  # rejected before anything was enqueued
+                    self._refuse(req, now, need, slot, f"rejected: {e}")
+                    continue
                 self._finish(req, now, need, slot, hits, [hits], k, stream)
         if traces:
             k, stream = self._stream()
@@ -219,7 +264,12 @@ class Server:
                     rays = torch.from_numpy(req.rays).to("cuda", non_blocking=True)
                     batch.append((vol, rays, hits))
                     launched.append((req, need, slot, hits, [hits, rays]))
-                trace_batch(batch, self.layout, stream=stream)
+                try:
+                    trace_batch(batch, self.layout, stream=stream)
+                except VxError as e:  # the batch is checked as a whole before launching
+                    for req, need, slot, _, _ in launched:
+                        self._refuse(req, now, need, slot, f"rejected: {e}")
+                    return
                 for req, need, slot, hits, keep in launched:
                     self._finish(req, now, need, slot, hits, keep, k, stream)
 

@@ -100,3 +100,30 @@ def test_serial_plain_path_same_results(volumes):
     res = serve.serve_serial(vols, reqs)
     for r in reqs:
         assert np.array_equal(res[r.id].hits, alone(vols, r))
+
+
+def test_bad_requests_are_refused_and_the_rest_served(volumes):
+    vols, grids = volumes
+    reqs = make_requests(14, 24, 0.02, grids)
+    good_cam = next(r.camera for r in reqs if r.camera is not None)
+    bad = [
+        serve.Request(900, "no_such_volume", 0.0, camera=dict(good_cam)),
+        serve.Request(901, "terrain_rsg", 0.0),                                   # neither camera nor rays
+        serve.Request(902, "terrain_rsg", 0.0, rays=np.zeros((100, 8), np.float64)),
+        serve.Request(903, "terrain_rsg", 0.0, rays=np.zeros((100, 7), np.float32)),
+        serve.Request(904, "terrain_rsg", 0.0, camera={k: v for k, v in good_cam.items() if k != "width"}),
+        serve.Request(905, "terrain_rsg", 0.0, camera=dict(good_cam, vfov_deg=0.0)),  # rejected by the library
+    ]
+    srv = serve.Server(vols, mem_budget_bytes=32 << 20, max_inflight=8)
+    res = srv.run(reqs + bad, realtime=False)
+    for b in bad[:5]:
+        assert res[b.id].refused.startswith("invalid request"), (b.id, res[b.id].refused)
+    assert res[905].refused.startswith("rejected")
+    for b in bad:
+        assert res[b.id].hits is None
+    for r in reqs:
+        assert res[r.id].refused is None
+        assert np.array_equal(res[r.id].hits, alone(vols, r)), r.id
+    # every byte of the budget and of the pinned download space came back
+    assert srv.used == 0 and srv.n_inflight == 0
+    assert srv.arena.free == [(0, srv.arena.nbytes)]
