@@ -315,7 +315,8 @@ int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layou
  * events on `stream` (each candidate the best of three launches) --
  * restarting vs stack traversal, top level in shared memory, coherence-sort
  * granularity, persistent refill threshold, iterations per refill check,
- * block size (two rounds), plain vs persistent -- by coordinate descent, and
+ * block size (two rounds), then the plain kernel at each block size -- by
+ * coordinate descent, and
  * keeps the fastest; later vx_trace calls with
  * opts NULL or mode VX_MODE_AUTO use it.  Synchronises `stream`; allocates a
  * temporary n-hit buffer.  best (optional) receives the options, best_ms the

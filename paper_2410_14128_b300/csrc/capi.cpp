@@ -472,7 +472,18 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
         for (int bu : {1, 2, 4, 8, 16, 32, 64}) { vx_trace_opts c = cur; c.burst = bu; consider(c); }
         for (int bl : {64, 128, 256}) { vx_trace_opts c = cur; c.block = bl; consider(c); }
     }
-    { vx_trace_opts c = cur; c.mode = VX_MODE_PLAIN; consider(c); }
+    // the one-thread-per-ray kernel (sorting and restarting carry over;
+    // shared-memory staging is a persistent-kernel option)
+    {
+        const vx_trace_opts p = cur;
+        for (int bl : {64, 128, 256}) {
+            vx_trace_opts c = p;
+            c.mode = VX_MODE_PLAIN;
+            c.smem_top = 0;
+            c.block = bl;
+            consider(c);
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(hits);
