@@ -217,8 +217,8 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
 
 /* Trace options (NULL = defaults / autotuned values).
  *   mode   VX_MODE_*;
- *   block  threads per block: 0 = default, else a multiple of 32 in
- *          [32, 256] (VX_EINVAL otherwise);
+ *   block  threads per block: 0 = default (256; 128 for the plain render
+ *          kernel), else a multiple of 32 in [32, 256] (VX_EINVAL otherwise);
  *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = as many as fit;
  *   smem_top  persistent mode: 1 = each block first copies the top level
  *          into shared memory and reads its cells there (a Raw or DF top
