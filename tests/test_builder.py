@@ -331,3 +331,16 @@ def test_load_rejects_corruption_anywhere():
         except vx.VxError:
             rejected += 1
     assert rejected >= 20  # most corruptions hit a pointer or a mask; RGBA words may take any value
+
+
+def test_load_refuses_buffers_beyond_the_word_limit():
+    # Sec. 3.3: 32-bit word offsets, so at most 2^32 - 1 words; the size is
+    # checked before any word is read (the 4-word array stands for a huge one)
+    import ctypes
+    w = np.zeros(4, np.uint32)
+    o = vx._BuildOpts(vx.DEDUP_WHOLE_LEVEL, -1, 1, 0, 0)
+    h = ctypes.c_void_p()
+    rc = vx.lib().vx_load(b"G(2)", ctypes.c_void_p(w.ctypes.data), 1 << 32, ctypes.byref(o), 1, ctypes.byref(h))
+    assert rc == vx.VX_ETOOBIG and not h.value
+    rc = vx.lib().vx_load(b"G(2)", ctypes.c_void_p(w.ctypes.data), 0, ctypes.byref(o), 1, ctypes.byref(h))
+    assert rc == vx.VX_EINVAL and not h.value
