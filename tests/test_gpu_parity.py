@@ -179,6 +179,16 @@ def test_terrain512_full_size_sampled(terrain512, spec):
     si = rng.choice(len(inc), 150000, replace=False)
     compare(g, prim[sp], hp[sp])
     compare(g, inc[si], hi[si])
+    # and in the benchmark's own configuration: the tiled render of the view,
+    # and the incoherent rays traced with the autotuned options
+    tuned = vol.autotune(torch.from_numpy(inc).cuda())
+    assert np.array_equal(gpu_trace(vol, inc), hi), tuned
+    hr = vx.alloc_hits(len(prim))
+    vol.render(cam, hr)
+    torch.cuda.synchronize()
+    hr = vx.hits_to_numpy(hr)
+    rg = vx.raygen_pinhole(cam).cpu().numpy()
+    compare(g, rg[sp], hr[sp])
 
 
 # ---------------------------------------------------------------------------
