@@ -97,6 +97,17 @@ def ncu_counters(kernel_key: str):
 ISSUE_PEAK_GINST_S = 148 * 4 * 2.032
 
 
+def trace_launches(opts: dict | None, log2_dim) -> int:
+    """Kernels one vx_trace call launches: the trace, plus the coherence sort
+    when the options ask for it (key histogram, tiled scan of the bins -- a
+    second pass when there is more than one tile of 8192 -- and scatter)."""
+    g = opts.get("sort_cell_log2", 0) if opts else 0
+    if not g:
+        return 1
+    nbins = 8 << sum(min(max(ld - g, 0), 5) for ld in log2_dim)
+    return 1 + 3 + (1 if nbins > 8192 else 0)
+
+
 def pcie_both_ways_gbs(nbytes: int = 256 << 20, reps: int = 5) -> float:
     """Host<->device copy rate (GB/s, both directions summed) with one
     pinned-host upload and one download in flight at once on two streams."""
@@ -258,6 +269,7 @@ def run_gpu(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     rays_per_step = len(FORMATS) * (n_prim + N_INC)
     mode = {"auto": vx.MODE_AUTO, "plain": vx.MODE_PLAIN, "persistent": vx.MODE_PERSISTENT}[args.mode]
+    fixed = {"sort": args.sort} if args.sort and mode != vx.MODE_AUTO else {}  # fixed options (no autotuning)
 
     # --- autotune the incoherent-ray trace per format (outside timing) ---
     tuned = []
@@ -303,7 +315,7 @@ def run_gpu(args):
                     if name == "render":
                         v.render(cam, hits_p[k])
                     else:
-                        v.trace(inc, hits_i[k], mode=mode)
+                        v.trace(inc, hits_i[k], mode=mode, **fixed)
                     if evs is not None:
                         evs[(k, name)][1].record(st)
         traced = torch.cuda.Event()
@@ -377,7 +389,7 @@ def run_gpu(args):
             if name == "render":
                 vols[k].render(cam, hits_p[k])
             else:
-                vols[k].trace(inc, hits_i[k], mode=mode)
+                vols[k].trace(inc, hits_i[k], mode=mode, **fixed)
             b.record()
             ts.append((a, b))
         torch.cuda.synchronize()
@@ -421,6 +433,9 @@ def run_gpu(args):
     else:
         persistent = mode == vx.MODE_PERSISTENT or (mode == vx.MODE_AUTO and (not tuned or tuned[k]["mode"] == "persistent"))
         kname = "k_trace_persistent" if persistent else "k_trace"
+        g_sort = tuned[k]["sort_cell_log2"] if tuned else fixed.get("sort", 0)
+        if g_sort:
+            kname += f"+sort{g_sort}"  # rays read through the sort's permutation
     # counters of the same kernel on the same format (a capture of another
     # kernel does not count)
     kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}:{kname}"
@@ -538,7 +553,9 @@ def run_gpu(args):
             "roofline_issue": roofline_issue,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * len(FORMATS) * args.steps,
+            "gpu_launches": args.steps * sum(1 + trace_launches(tuned[k] if tuned else {"sort_cell_log2": fixed.get("sort", 0)},
+                                                                vols[k].log2_dim)
+                                             for k in range(len(FORMATS))),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -920,6 +937,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--mode", default="auto", choices=["auto", "plain", "persistent"])
+    ap.add_argument("--sort", type=int, default=0,
+                    help="with --mode plain/persistent: sort the incoherent rays by origin cells of side 2^G")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

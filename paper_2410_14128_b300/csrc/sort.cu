@@ -54,28 +54,71 @@ __global__ void __launch_bounds__(256) k_sort_hist(const float4* __restrict__ ra
     atomicAdd(hist + key, 1u);
 }
 
-// In-place exclusive scan of `nbins` counters with one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* __restrict__ hist, uint32_t nbins) {
-    __shared__ uint32_t part[1024];
-    const uint32_t t = threadIdx.x;
-    const uint32_t per = (nbins + 1023) / 1024;
-    const uint32_t lo = t * per, hi = min(lo + per, nbins);
-    uint32_t sum = 0;
-    for (uint32_t i = lo; i < hi; i++) sum += hist[i];
-    part[t] = sum;
+// Exclusive scan of the `nbins` counters in tiles of kScanTile: each block
+// scans one tile in shared memory (loads and stores coalesced; a thread owns
+// 8 consecutive counters) and records the tile's total; a second launch adds
+// the totals of the earlier tiles.  nbins <= 2^18, so at most 32 tiles.
+constexpr uint32_t kScanTile = 8192;
+constexpr uint32_t kScanMaxTiles = 32;
+
+__global__ void __launch_bounds__(1024) k_sort_scan_tiles(uint32_t* __restrict__ hist, uint32_t nbins,
+                                                          uint32_t* __restrict__ tile_sums) {
+    __shared__ uint32_t s[kScanTile];
+    __shared__ uint32_t warp_excl[32];
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t base = blockIdx.x * kScanTile;
+    for (uint32_t k = t; k < kScanTile; k += 1024) s[k] = base + k < nbins ? hist[base + k] : 0u;
     __syncthreads();
-    for (uint32_t off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = t >= off ? part[t - off] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        v[k] = s[t * 8 + k];
+        sum += v[k];
     }
-    uint32_t run = part[t] - sum;  // exclusive prefix of this thread's chunk
-    for (uint32_t i = lo; i < hi; i++) {
-        const uint32_t c = hist[i];
-        hist[i] = run;
-        run += c;
+    uint32_t incl = sum;  // inclusive scan of the threads' sums within the warp
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
+    if (lane == 31) warp_excl[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = warp_excl[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_excl[lane] = wi - w;
+        if (lane == 31) tile_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_excl[warp] + incl - sum;  // counters before this thread's 8 in the tile
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        s[t * 8 + k] = run;
+        run += v[k];
+    }
+    __syncthreads();
+    for (uint32_t k = t; k < kScanTile; k += 1024)
+        if (base + k < nbins) hist[base + k] = s[k];
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan_add(uint32_t* __restrict__ hist, uint32_t nbins,
+                                                        const uint32_t* __restrict__ tile_sums) {
+    __shared__ uint32_t off;
+    if (threadIdx.x < 32) {
+        uint32_t x = threadIdx.x < blockIdx.x ? tile_sums[threadIdx.x] : 0u;
+#pragma unroll
+        for (uint32_t o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (threadIdx.x == 0) off = x;
+    }
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kScanTile;
+    for (uint32_t k = threadIdx.x; k < kScanTile; k += 1024)
+        if (base + k < nbins) hist[base + k] += off;
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(const uint32_t* __restrict__ keys, uint64_t n,
@@ -83,7 +126,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(const uint32_t* __restrict
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t pos = atomicAdd(offsets + keys[i], 1u);
-    order[pos] = (uint32_t)i;
+    if (pos < n) order[pos] = (uint32_t)i;  // always true when the offsets are right
 }
 
 }  // namespace
@@ -99,7 +142,7 @@ uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbin
     }
     const uint32_t nbins = 8u << mbits;
     if (nbins_out) *nbins_out = nbins;
-    return 2 * n * sizeof(uint32_t) + (uint64_t)nbins * sizeof(uint32_t) + 256;
+    return 2 * n * sizeof(uint32_t) + ((uint64_t)nbins + kScanMaxTiles) * sizeof(uint32_t) + 256;
 }
 
 // Fills order[0..n) (inside `scratch`) with ray indices sorted by key.
@@ -121,11 +164,14 @@ int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* sc
     uint32_t* keys = static_cast<uint32_t*>(scratch);
     uint32_t* order = keys + n;
     uint32_t* hist = order + n;
+    uint32_t* tile_sums = hist + nbins;
+    const uint32_t tiles = (nbins + kScanTile - 1) / kScanTile;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nbins * sizeof(uint32_t), st);
     if (e) return fail(VX_ECUDA, "sort memset: %s", cudaGetErrorString(e));
     const unsigned grid = (unsigned)((n + 255) / 256);
     k_sort_hist<<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(rays), n, kp, keys, hist);
-    k_sort_scan<<<1, 1024, 0, st>>>(hist, nbins);
+    k_sort_scan_tiles<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
+    if (tiles > 1) k_sort_scan_add<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
     k_sort_scatter<<<grid, 256, 0, st>>>(keys, n, hist, order);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "sort launch: %s", cudaGetErrorString(e));
