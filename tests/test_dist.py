@@ -46,3 +46,17 @@ def test_two_rank_throughput_gloo():
         assert total_ms == 200.0  # max over ranks
         assert value == pytest.approx(2 * 1_000_000 / 0.2 / 1e6)  # whole job: 10 Mrays/s
         assert info == (rank, 0, world)
+
+
+def test_launch_count_includes_the_sort():
+    # gpu_launches counts the sort's kernels when the options sort: histogram,
+    # scan of 8192-bin tiles (plus a second pass past one tile), scatter
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    d = (9, 9, 9)
+    assert bench.trace_launches(None, d) == 1
+    assert bench.trace_launches({"sort_cell_log2": 0}, d) == 1
+    assert bench.trace_launches({"sort_cell_log2": 6}, d) == 4   # 8 x 8^3 = 4096 bins: one tile
+    assert bench.trace_launches({"sort_cell_log2": 4}, d) == 5   # 8 x 32^3 bins: several tiles
+    assert bench.trace_launches({"sort_cell_log2": 9}, d) == 4   # one cell: 8 bins
