@@ -383,8 +383,8 @@ int vx_raygen_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed
                  vx_ray* out, void* stream);
 
 /* Pinhole rays generated and traced in one kernel (no ray array in memory);
- * hits as for vx_trace, one per pixel (hit k = pixel x + width * y, k = x +
- * width * y).  opts: mode VX_MODE_PLAIN (one thread per pixel, each warp an
+ * hits as for vx_trace, one per pixel (hit x + width * y belongs to pixel
+ * (x, y)).  opts: mode VX_MODE_PLAIN (one thread per pixel, each warp an
  * 8 x 4 pixel tile, blocks of 128 by default; the default mode, also for
  * NULL / AUTO) or VX_MODE_PERSISTENT (pixels taken in row order from a queue
  * by persistent warps); refill, burst, block as for vx_trace (the volume's
