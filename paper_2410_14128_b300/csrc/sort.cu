@@ -45,13 +45,16 @@ __device__ __forceinline__ uint32_t ray_key(const float4 a, const float4 b, cons
     return (oct << k.mbits) | m;
 }
 
+// Key of each ray, and its rank among the rays of its bin (the count the
+// atomic returns), so the scatter needs no atomics of its own.
 __global__ void __launch_bounds__(256) k_sort_hist(const float4* __restrict__ rays, uint64_t n, KeyParams kp,
-                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ ranks,
+                                                   uint32_t* __restrict__ hist) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t key = ray_key(__ldg(rays + 2 * i), __ldg(rays + 2 * i + 1), kp);
     keys[i] = key;
-    atomicAdd(hist + key, 1u);
+    ranks[i] = atomicAdd(hist + key, 1u);
 }
 
 // Exclusive scan of the `nbins` counters in tiles of kScanTile: each block
@@ -121,11 +124,13 @@ __global__ void __launch_bounds__(1024) k_sort_scan_add(uint32_t* __restrict__ h
         if (base + k < nbins) hist[base + k] += off;
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(const uint32_t* __restrict__ keys, uint64_t n,
-                                                      uint32_t* __restrict__ offsets, uint32_t* __restrict__ order) {
+__global__ void __launch_bounds__(256) k_sort_scatter(const uint32_t* __restrict__ keys,
+                                                      const uint32_t* __restrict__ ranks, uint64_t n,
+                                                      const uint32_t* __restrict__ offsets,
+                                                      uint32_t* __restrict__ order) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t pos = atomicAdd(offsets + keys[i], 1u);
+    const uint32_t pos = __ldg(offsets + keys[i]) + ranks[i];
     if (pos < n) order[pos] = (uint32_t)i;  // always true when the offsets are right
 }
 
@@ -142,7 +147,7 @@ uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbin
     }
     const uint32_t nbins = 8u << mbits;
     if (nbins_out) *nbins_out = nbins;
-    return 2 * n * sizeof(uint32_t) + ((uint64_t)nbins + kScanMaxTiles) * sizeof(uint32_t) + 256;
+    return 3 * n * sizeof(uint32_t) + ((uint64_t)nbins + kScanMaxTiles) * sizeof(uint32_t) + 256;
 }
 
 // Fills order[0..n) (inside `scratch`) with ray indices sorted by key.
@@ -162,17 +167,18 @@ int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* sc
     }
     const uint32_t nbins = 8u << kp.mbits;
     uint32_t* keys = static_cast<uint32_t*>(scratch);
-    uint32_t* order = keys + n;
+    uint32_t* ranks = keys + n;
+    uint32_t* order = ranks + n;
     uint32_t* hist = order + n;
     uint32_t* tile_sums = hist + nbins;
     const uint32_t tiles = (nbins + kScanTile - 1) / kScanTile;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nbins * sizeof(uint32_t), st);
     if (e) return fail(VX_ECUDA, "sort memset: %s", cudaGetErrorString(e));
     const unsigned grid = (unsigned)((n + 255) / 256);
-    k_sort_hist<<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(rays), n, kp, keys, hist);
+    k_sort_hist<<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(rays), n, kp, keys, ranks, hist);
     k_sort_scan_tiles<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
     if (tiles > 1) k_sort_scan_add<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
-    k_sort_scatter<<<grid, 256, 0, st>>>(keys, n, hist, order);
+    k_sort_scatter<<<grid, 256, 0, st>>>(keys, ranks, n, hist, order);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "sort launch: %s", cudaGetErrorString(e));
     *order_out = order;
