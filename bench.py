@@ -95,6 +95,7 @@ def ncu_counters(kernel_key: str):
 # Warp-instruction issue peak: 148 SMs x 4 schedulers x 1 warp instruction per
 # cycle at the 2032 MHz maximum SM clock.
 ISSUE_PEAK_GINST_S = 148 * 4 * 2.032
+NOMINAL_HBM_GBS = 8000.0  # B300 HBM3e, nominal (the measured copy rate is the roofline's peak)
 
 
 def trace_launches(opts: dict | None, log2_dim) -> int:
@@ -446,6 +447,7 @@ def run_gpu(args):
     compulsory = counts[dom]["footprint_bytes"] + n_rays * io
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "dram_frac": round(traffic / (avg_ms / 1e3) / 1e9 / peak, 4) if traffic else None,
                 "compulsory_bytes_per_launch": int(compulsory),
                 "kernel": f"{kname} {FORMATS[k]}",
