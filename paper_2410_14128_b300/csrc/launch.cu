@@ -164,7 +164,10 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     int e;
     if (mode == VX_MODE_PERSISTENT) {
         unsigned long long* next = v.queue_counter();
-        if (!next) return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+        if (!next) {
+            if (scratch) cudaFreeAsync(scratch, st);
+            return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+        }
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
