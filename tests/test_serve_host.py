@@ -1,6 +1,7 @@
 """Host-side logic of the serving loop (no GPU): the pinned download arena's
 first-fit allocator keeps its free list sorted, disjoint and merged, and
-never hands out overlapping slots."""
+never hands out overlapping slots; and requests are validated before they
+take memory."""
 import random
 
 from paper_2410_14128_b300.serve import HostArena
@@ -45,3 +46,30 @@ def test_arena_refuses_what_does_not_fit():
     a.release(*x)
     assert a.alloc(1024) == (0, 1024)
     a.release(*y)
+
+
+def test_request_validation_on_the_host():
+    # the checks a request passes before it takes memory (Server.invalid),
+    # run without a device on a stand-in server that only has volumes
+    import numpy as np
+    from paper_2410_14128_b300.serve import Request, Server
+    srv = object.__new__(Server)
+    srv.volumes = {"v": object()}
+    cam = {"eye": (1, 2, 3), "look": (0, 0, 0), "up": (0, 1, 0), "vfov_deg": 60.0, "width": 64, "height": 32}
+    ok_rays = np.zeros((10, 8), np.float32)
+    assert srv.invalid(Request(0, "v", 0.0, camera=cam)) is None
+    assert srv.invalid(Request(1, "v", 0.0, rays=ok_rays)) is None
+    bad = {
+        "unknown volume": Request(2, "w", 0.0, camera=cam),
+        "exactly one": Request(3, "v", 0.0),
+        "exactly one ": Request(4, "v", 0.0, camera=cam, rays=ok_rays),
+        "(n, 8) float32": Request(5, "v", 0.0, rays=np.zeros((10, 8), np.float64)),
+        "(n, 8) float32 ": Request(6, "v", 0.0, rays=np.zeros((10, 7), np.float32)),
+        "C-contiguous": Request(7, "v", 0.0, rays=np.zeros((8, 10), np.float32).T),
+        "bad camera": Request(8, "v", 0.0, camera={k: v for k, v in cam.items() if k != "vfov_deg"}),
+        "3 components": Request(9, "v", 0.0, camera=dict(cam, up=(0, 1))),
+        "empty": Request(10, "v", 0.0, camera=dict(cam, width=0)),
+    }
+    for want, req in bad.items():
+        why = srv.invalid(req)
+        assert why is not None and want.strip() in why, (want, why)
