@@ -177,28 +177,6 @@ int vx_free(vx_volume v);
 int vx_load(const char* spec, const uint32_t* words, uint64_t n_words, const vx_build_opts* opts, int32_t validate,
             vx_volume* out);
 
-/* Size and build statistics of a volume.  Level k counts the words written
- * for its structures (Raw arrays, octree node lists, DAG nodes) and its
- * nodes: Raw sub-volumes, or octree / DAG nodes including leaf nodes. */
-#define VX_MAX_LEVELS 16
-typedef struct vx_stats {
-    uint32_t n_levels;
-    uint32_t n_node_levels;  /* levels after expanding S(L)/G(L) into L octree levels */
-    uint32_t log2_dim[3];
-    int32_t specialized;     /* 1 = a compile-time-composed kernel serves this spec */
-    int32_t packed;          /* 1 = the device image uses the packed layout */
-    int32_t pad;
-    uint64_t canonical_words;   /* paper-layout buffer size in words */
-    uint64_t device_bytes;      /* device image size */
-    uint64_t occupied_voxels;
-    uint64_t level_words[VX_MAX_LEVELS];
-    uint64_t level_nodes[VX_MAX_LEVELS];
-    double build_ms;
-    double upload_ms;
-} vx_stats;
-
-int vx_stats_get(vx_volume v, vx_stats* out);
-
 /* Host view of the canonical (paper-layout) word buffer: word 0 is the root
  * pointer (Sec. 4.1).  The pointer stays valid until vx_free. */
 int vx_canonical(vx_volume v, const uint32_t** words, uint64_t* n_words);
@@ -252,6 +230,30 @@ typedef struct vx_trace_opts {
     int32_t sort_cell_log2;
     int32_t restart;
 } vx_trace_opts;
+
+/* Size and build statistics of a volume.  Level k counts the words written
+ * for its structures (Raw arrays, octree node lists, DAG nodes) and its
+ * nodes: Raw sub-volumes, or octree / DAG nodes including leaf nodes. */
+#define VX_MAX_LEVELS 16
+typedef struct vx_stats {
+    uint32_t n_levels;
+    uint32_t n_node_levels;  /* levels after expanding S(L)/G(L) into L octree levels */
+    uint32_t log2_dim[3];
+    int32_t specialized;     /* 1 = a compile-time-composed kernel serves this spec */
+    int32_t packed;          /* 1 = the device image uses the packed layout */
+    int32_t pad;
+    uint64_t canonical_words;   /* paper-layout buffer size in words */
+    uint64_t device_bytes;      /* device image size */
+    uint64_t occupied_voxels;
+    uint64_t level_words[VX_MAX_LEVELS];
+    uint64_t level_nodes[VX_MAX_LEVELS];
+    double build_ms;
+    double upload_ms;
+    int32_t tuned;              /* 1 once vx_autotune has chosen options */
+    vx_trace_opts tuned_opts;   /* the options VX_MODE_AUTO traces use (valid when tuned) */
+} vx_stats;
+
+int vx_stats_get(vx_volume v, vx_stats* out);
 
 /* First hit of each ray (Sec. 4.2: the root function reads the root pointer,
  * tests the root box and calls the level functions, which visit non-empty

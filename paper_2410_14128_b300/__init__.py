@@ -52,19 +52,20 @@ class _BuildOpts(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("canonical_device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
+class _TraceOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
+                ("sort_cell_log2", ctypes.c_int32), ("restart", ctypes.c_int32)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_uint32), ("n_node_levels", ctypes.c_uint32), ("log2_dim", ctypes.c_uint32 * 3),
                 ("specialized", ctypes.c_int32), ("packed", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("canonical_words", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("occupied_voxels", ctypes.c_uint64),
                 ("level_words", ctypes.c_uint64 * MAX_LEVELS), ("level_nodes", ctypes.c_uint64 * MAX_LEVELS),
-                ("build_ms", ctypes.c_double), ("upload_ms", ctypes.c_double)]
-
-
-class _TraceOpts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
-                ("sort_cell_log2", ctypes.c_int32), ("restart", ctypes.c_int32)]
+                ("build_ms", ctypes.c_double), ("upload_ms", ctypes.c_double),
+                ("tuned", ctypes.c_int32), ("tuned_opts", _TraceOpts)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -148,6 +149,12 @@ def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, r
     o.sort_cell_log2 = sort
     o.restart = int(restart)
     return o
+
+
+def _opts_dict(o: _TraceOpts) -> dict:
+    return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
+            "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
+            "smem_top": bool(o.smem_top)}
 
 
 def _camera(cam: dict) -> _Camera:
@@ -305,6 +312,7 @@ class Volume:
             "canonical_bytes": 4 * s.canonical_words, "device_bytes": s.device_bytes,
             "occupied_voxels": s.occupied_voxels, "level_words": list(s.level_words)[:n],
             "level_nodes": list(s.level_nodes)[:n], "build_ms": s.build_ms, "upload_ms": s.upload_ms,
+            "tuned": _opts_dict(s.tuned_opts) if s.tuned else None,
         }
 
     def canonical(self) -> np.ndarray:
@@ -361,10 +369,7 @@ class Volume:
         ms = ctypes.c_double()
         _check(lib().vx_autotune(self._h, ctypes.c_void_p(sample_rays.data_ptr()), sample_rays.shape[0],
                                  _stream_handle(stream), ctypes.byref(o), ctypes.byref(ms)))
-        return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
-                "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
-                "smem_top": bool(o.smem_top),
-                "sample_ms": ms.value}
+        return dict(_opts_dict(o), sample_ms=ms.value)
 
     def trace_host(self, rays: np.ndarray, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,
                    **opts) -> np.ndarray:

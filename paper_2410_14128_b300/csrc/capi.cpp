@@ -304,6 +304,9 @@ extern "C" int vx_stats_get(vx_volume v, vx_stats* out) {
     clear_error();
     if (!v || !out) return fail(VX_EINVAL, "NULL argument");
     *out = v->v.stats;
+    std::lock_guard<std::mutex> lock(v->v.tune_mu);
+    out->tuned = v->v.tuned ? 1 : 0;
+    out->tuned_opts = v->v.tuned ? v->v.tuned_opts : vx_trace_opts{};
     return VX_OK;
 }
 

@@ -53,6 +53,31 @@ def test_binding_argument_counts_match_header():
         assert len(vx._SIGS[name][1]) == count, name
 
 
+def test_struct_layouts_match_header(tmp_path):
+    # the ctypes mirrors of the C structs have the header's sizes and offsets
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "vx.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(vx_stats), '
+                   'offsetof(vx_stats, upload_ms), offsetof(vx_stats, tuned), offsetof(vx_stats, tuned_opts), '
+                   'sizeof(vx_trace_opts), sizeof(vx_batch_item)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(vx._Stats), vx._Stats.upload_ms.offset, vx._Stats.tuned.offset,
+            vx._Stats.tuned_opts.offset, ctypes.sizeof(vx._TraceOpts), ctypes.sizeof(vx._BatchItem)]
+    assert got == want
+
+
+def test_stats_report_no_tuning_before_autotune():
+    g = synth.random_grid(5, (16, 16, 16), 0.2)
+    assert build("R(2,2,2) S(2)", g).stats()["tuned"] is None
+
+
 def test_footprint_bytes_counts_marked_sectors():
     torch = pytest.importorskip("torch")
     words = np.zeros(5, np.uint32)

@@ -336,8 +336,10 @@ def test_autotune_keeps_results():
     rays = synth.incoherent_rays(86, 128, 200000)
     vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
     ref = gpu_trace(vol, rays, mode=vx.MODE_PLAIN)
+    assert vol.stats()["tuned"] is None
     best = vol.autotune(torch.from_numpy(rays[:100000]).cuda())
     assert best["mode"] in ("plain", "persistent") and best["sample_ms"] > 0
+    assert vol.stats()["tuned"] == {k: v for k, v in best.items() if k != "sample_ms"}
     assert np.array_equal(gpu_trace(vol, rays), ref)  # default mode now uses the tuned options
 
 
