@@ -4,7 +4,8 @@
  * NVIDIA B300 (sm_103a).
  *
  * A hybrid format is a list of levels, each one of the paper's base formats
- * (Sec. 3.1, Table 1): Raw R(W,H,D), SVO S(L) or SVDAG G(L).  A voxel holds a
+ * (Sec. 3.1, Table 1): Raw R(W,H,D), distance field D(W,H,D,M), SVO S(L) or
+ * SVDAG G(L).  A voxel holds a
  * 32-bit RGBA word (R | G << 8 | B << 16 | A << 24) and is empty iff all 32
  * bits are 0 (Sec. 3).  The library builds a volume in the paper's word-buffer
  * layout (Sec. 3.3, Fig. 3) with the Morton-order construction of Sec. 4.1 and
@@ -172,8 +173,10 @@ int vx_free(vx_volume v);
  * entry point then refuses it (VX_EINVAL) except vx_trace_counted, whose
  * reads are checked.  opts as for vx_build (dedup_scope and threads unused).
  * Stats: canonical_words and per-level words / node counts (from the walk),
- * occupied_voxels 0.  The paper has no loader: its construction writes the
- * buffer to a file (Sec. 4.1); this reads such a buffer back. */
+ * occupied_voxels 0.  Errors: VX_EINVAL (spec, empty or malformed buffer),
+ * VX_ETOOBIG (n_words >= 2^32, checked before any word is read), VX_ENOMEM,
+ * VX_ECUDA.  The paper has no loader: its construction writes the buffer to
+ * a file (Sec. 4.1); this reads such a buffer back. */
 int vx_load(const char* spec, const uint32_t* words, uint64_t n_words, const vx_build_opts* opts, int32_t validate,
             vx_volume* out);
 
