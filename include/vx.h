@@ -5,9 +5,8 @@
  *
  * A hybrid format is a list of levels, each one of the paper's base formats
  * (Sec. 3.1, Table 1): Raw R(W,H,D), distance field D(W,H,D,M), SVO S(L) or
- * SVDAG G(L).  A voxel holds a
- * 32-bit RGBA word (R | G << 8 | B << 16 | A << 24) and is empty iff all 32
- * bits are 0 (Sec. 3).  The library builds a volume in the paper's word-buffer
+ * SVDAG G(L).  A voxel holds a 32-bit RGBA word (R | G << 8 | B << 16 |
+ * A << 24) and is empty iff all 32 bits are 0 (Sec. 3).  The library builds a volume in the paper's word-buffer
  * layout (Sec. 3.3, Fig. 3) with the Morton-order construction of Sec. 4.1 and
  * Sec. 5, copies it to the GPU, and answers first-hit ray queries with CUDA
  * kernels whose per-level steppers are composed at compile time (Sec. 4.2).
