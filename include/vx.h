@@ -136,14 +136,20 @@ typedef struct vx_grid {
  *                 24..31 and an SVDAG slot of a leaf child holds the leaf's
  *                 terminating integer, which saves one or two dependent reads
  *                 per SVDAG level (vx_canonical always returns the paper's
- *                 layout). */
+ *                 layout);
+ *   generic_kernel  1 = trace with the kernels that take the format as a
+ *                 run-time argument even when a compile-time-composed kernel
+ *                 exists for the spec (same results; for checking the two
+ *                 against each other); 0 (default) = the compile-time kernel
+ *                 when one is compiled in (see vx_formats). */
 typedef struct vx_build_opts {
     int32_t dedup_scope;
     int32_t device;
     int32_t no_upload;
     int32_t threads;
     int32_t canonical_device;
-    int32_t reserved[3];
+    int32_t generic_kernel;
+    int32_t reserved[2];
 } vx_build_opts;
 
 /* Builds `spec` over `grid` and uploads it.  Paper: Sec. 4.1 (per-level
@@ -156,6 +162,18 @@ typedef struct vx_build_opts {
  * Errors: VX_EINVAL (spec or grid), VX_ETOOBIG (over 2^32 words, Sec. 3.3),
  * VX_ENOMEM, VX_ECUDA, VX_EUNSUPPORTED (a level kind this build lacks). */
 int vx_build(const char* spec, const vx_grid* grid, const vx_build_opts* opts, vx_volume* out);
+
+/* Signatures of the formats whose kernels are composed at compile time
+ * (Sec. 4: the paper generates one intersection function per level of a
+ * format; here C++ templates fold each listed format into constants).  Any
+ * other valid signature is traced by the kernels that read the format as a
+ * run-time argument.
+ *   specs     NULL, or an array of `capacity` pointers that receives the
+ *             first min(capacity, count) signatures, in the canonical
+ *             spelling vx_build accepts (static strings, never freed);
+ *   count     receives the number of compiled-in formats.
+ * Errors: VX_EINVAL (count NULL). */
+int vx_formats(const char** specs, uint32_t capacity, uint32_t* count);
 
 /* Releases the host and device memory of a volume (synchronises its device
  * first).  NULL is accepted. */
@@ -313,6 +331,19 @@ typedef struct vx_batch_item {
 } vx_batch_item;
 int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
                    void* stream);
+
+/* vx_trace_batch that also times its kernels: it records caller-created
+ * CUDA events (cudaEvent_t, created with timing enabled) on the stream each
+ * group's kernel runs on, events[2k] just before group k's kernel and
+ * events[2k + 1] just after it, so cudaEventElapsedTime of the pair is that
+ * kernel's duration.  Groups are numbered in the order their first set
+ * appears in `items` (a format with more than 64 sets forms several groups,
+ * consecutive); groups k >= n_events / 2 are not timed.  *groups (optional)
+ * receives the number of groups launched.  Capturable like vx_trace_batch
+ * (the records become event nodes of the graph).  Errors as vx_trace_batch,
+ * plus VX_EINVAL for n_events > 0 with events NULL. */
+int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
+                         void* stream, void** events, uint32_t n_events, uint32_t* groups);
 
 /* Picks vx_trace options for this volume: times candidates on `rays` (a
  * device sample of the rays the caller will trace, n of them) with CUDA

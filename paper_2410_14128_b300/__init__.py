@@ -49,7 +49,8 @@ class _Grid(ctypes.Structure):
 
 class _BuildOpts(ctypes.Structure):
     _fields_ = [("dedup_scope", ctypes.c_int32), ("device", ctypes.c_int32), ("no_upload", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("canonical_device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("threads", ctypes.c_int32), ("canonical_device", ctypes.c_int32), ("generic_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class _TraceOpts(ctypes.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "vx_build": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_Grid), ctypes.POINTER(_BuildOpts),
                                 ctypes.POINTER(ctypes.c_void_p)]),
     "vx_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "vx_formats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "vx_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(_BuildOpts),
                                ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "vx_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Stats)]),
@@ -98,6 +100,10 @@ _SIGS = {
                                         ctypes.c_void_p]),
     "vx_trace_batch": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
                                       ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_trace_batch_timed": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
+                                            ctypes.POINTER(_TraceOpts), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                                            ctypes.POINTER(ctypes.c_uint32)]),
     "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                    ctypes.POINTER(_TraceOpts), ctypes.POINTER(ctypes.c_double)]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -140,6 +146,16 @@ def exported_symbols():
 def _check(rc: int):
     if rc != VX_OK:
         raise VxError(rc, lib().vx_last_error().decode(errors="replace"))
+
+
+def compiled_formats() -> list[str]:
+    """Signatures whose kernels are composed at compile time (vx_formats)."""
+    L = lib()
+    n = ctypes.c_uint32()
+    _check(L.vx_formats(None, 0, ctypes.byref(n)))
+    arr = (ctypes.c_char_p * max(1, n.value))()
+    _check(L.vx_formats(arr, n.value, ctypes.byref(n)))
+    return [arr[i].decode() for i in range(n.value)]
 
 
 def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False, smem_top=False):
@@ -197,11 +213,14 @@ class Volume:
 
     def __init__(self, spec: str, grid: np.ndarray | None = None, *, palette=None, log2_dim=None,
                  fill_brick=None, block_empty=None, user=None, dedup: int = DEDUP_WHOLE_LEVEL, device: int = -1,
-                 upload: bool = True, canonical_device: bool = False, threads: int = 0):
+                 upload: bool = True, canonical_device: bool = False, threads: int = 0,
+                 generic_kernel: bool = False):
         """grid: dense (nz, ny, nx) uint32 RGBA array, or uint8 palette
         indices with `palette` (256 words); or log2_dim + fill_brick (a Python
         callable, or the address of a C function with the vx_fill_brick_fn
-        signature) with optional block_empty and user."""
+        signature) with optional block_empty and user.  generic_kernel: trace
+        with the kernels that read the format at run time even when a
+        compile-time-composed kernel exists (for comparing the two)."""
         L = lib()
         g = _Grid()
         self._keep = []
@@ -241,7 +260,8 @@ class Volume:
                 g.user = user.value if isinstance(user, ctypes.c_void_p) else user
         for i in range(3):
             g.log2_dim[i] = dims[i]
-        o = _BuildOpts(dedup, device, 0 if upload else 1, threads, 1 if canonical_device else 0)
+        o = _BuildOpts(dedup, device, 0 if upload else 1, threads, 1 if canonical_device else 0,
+                       1 if generic_kernel else 0)
         h = ctypes.c_void_p()
         _check(L.vx_build(spec.encode(), ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -251,7 +271,7 @@ class Volume:
 
     @classmethod
     def load(cls, spec: str, words: np.ndarray, *, validate: bool = True, device: int = -1, upload: bool = True,
-             canonical_device: bool = False) -> "Volume":
+             canonical_device: bool = False, generic_kernel: bool = False) -> "Volume":
         """A volume from a word buffer in the paper's layout (e.g. `canonical()`
         of another volume, or `words` of a file written by `save`).  With
         validate=False only `trace_counted` may trace it (its reads are
@@ -259,7 +279,8 @@ class Volume:
         w = np.ascontiguousarray(words, dtype=np.uint32)
         self = cls.__new__(cls)
         self._keep = []
-        o = _BuildOpts(DEDUP_WHOLE_LEVEL, device, 0 if upload else 1, 0, 1 if canonical_device else 0)
+        o = _BuildOpts(DEDUP_WHOLE_LEVEL, device, 0 if upload else 1, 0, 1 if canonical_device else 0,
+                       1 if generic_kernel else 0)
         h = ctypes.c_void_p()
         _check(lib().vx_load(spec.encode(), ctypes.c_void_p(w.ctypes.data), w.size, ctypes.byref(o), int(validate),
                              ctypes.byref(h)))
@@ -401,8 +422,12 @@ class Volume:
         return out
 
 
-def trace_batch(items, layout: int = HIT_FULL, stream=None, **opts):
-    """items: list of (Volume, rays tensor, hits tensor); one vx_trace_batch call."""
+def trace_batch(items, layout: int = HIT_FULL, stream=None, events=None, **opts) -> int:
+    """items: list of (Volume, rays tensor, hits tensor); one vx_trace_batch
+    call.  events: optional list of timing-enabled torch.cuda.Event, recorded
+    in pairs around each group's kernel on the stream it runs on
+    (vx_trace_batch_timed).  Returns the number of groups launched (0 when
+    not timed)."""
     arr = (_BatchItem * max(1, len(items)))()
     for k, (vol, rays, hits) in enumerate(items):
         arr[k].volume = vol.handle
@@ -410,8 +435,17 @@ def trace_batch(items, layout: int = HIT_FULL, stream=None, **opts):
         arr[k].n = rays.shape[0]
         arr[k].hits = hits.data_ptr()
     o = _opts(**opts) if opts else None
-    _check(lib().vx_trace_batch(arr, len(items), layout, ctypes.byref(o) if o is not None else None,
-                                _stream_handle(stream)))
+    op = ctypes.byref(o) if o is not None else None
+    if events is None:
+        _check(lib().vx_trace_batch(arr, len(items), layout, op, _stream_handle(stream)))
+        return 0
+    if any(not e.cuda_event for e in events):
+        raise ValueError("record each event once (creating it) before passing it to trace_batch")
+    ev = (ctypes.c_void_p * max(1, len(events)))(*[e.cuda_event for e in events])
+    groups = ctypes.c_uint32()
+    _check(lib().vx_trace_batch_timed(arr, len(items), layout, op, _stream_handle(stream), ev, len(events),
+                                      ctypes.byref(groups)))
+    return groups.value
 
 
 def raygen_ao(rays, hits, seed: int, spp: int = 8, eps: float = 1e-3, tmax: float = 32.0, out=None, stream=None):

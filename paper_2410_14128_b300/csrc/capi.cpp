@@ -197,7 +197,7 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
             return fail(VX_EINVAL, "spec '%s' describes a 2^%d x 2^%d x 2^%d grid, the grid is 2^%u x 2^%u x 2^%u",
                         spec, sp.ldim[0], sp.ldim[1], sp.ldim[2], grid->log2_dim[0], grid->log2_dim[1],
                         grid->log2_dim[2]);
-    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, {0, 0, 0}};
+    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, 0, {0, 0}};
     if (opts) o = *opts;
     if (o.dedup_scope != VX_DEDUP_WHOLE_LEVEL && o.dedup_scope != VX_DEDUP_PER_SUBVOLUME)
         return fail(VX_EINVAL, "bad dedup_scope %d", o.dedup_scope);
@@ -225,7 +225,7 @@ extern "C" int vx_build(const char* spec, const vx_grid* grid, const vx_build_op
         st.level_nodes[k] = V.built.level_nodes[k];
     }
     st.build_ms = t1 - t0;
-    V.kernels = kernels_for(sp);
+    V.kernels = o.generic_kernel ? generic_kernels() : kernels_for(sp);
     st.specialized = kernel_set_specialized(V.kernels) ? 1 : 0;
 
     if (!o.no_upload) {
@@ -247,7 +247,7 @@ extern "C" int vx_load(const char* spec, const uint32_t* words, uint64_t n_words
     Spec sp;
     int rc = parse_spec(spec, &sp);
     if (rc) return rc;
-    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, {0, 0, 0}};
+    vx_build_opts o{VX_DEDUP_WHOLE_LEVEL, -1, 0, 0, 0, 0, {0, 0}};
     if (opts) o = *opts;
     std::unique_ptr<vx_volume_s> h(new vx_volume_s);
     Volume& V = h->v;
@@ -271,7 +271,7 @@ extern "C" int vx_load(const char* spec, const uint32_t* words, uint64_t n_words
         st.level_nodes[k] = V.built.level_nodes[k];
     }
     st.build_ms = now_ms() - t0;
-    V.kernels = kernels_for(sp);
+    V.kernels = o.generic_kernel ? generic_kernels() : kernels_for(sp);
     st.specialized = kernel_set_specialized(V.kernels) ? 1 : 0;
     if (!o.no_upload) {
         const double t1 = now_ms();
@@ -281,6 +281,16 @@ extern "C" int vx_load(const char* spec, const uint32_t* words, uint64_t n_words
         st.upload_ms = now_ms() - t1;
     }
     *out = h.release();
+    return VX_OK;
+}
+
+extern "C" int vx_formats(const char** specs, uint32_t capacity, uint32_t* count) {
+    clear_error();
+    if (!count) return fail(VX_EINVAL, "count is NULL");
+    const std::vector<const KernelSet*> all = registered_kernel_sets();
+    *count = (uint32_t)all.size();
+    if (specs)
+        for (uint32_t i = 0; i < capacity && i < all.size(); i++) specs[i] = kernel_set_spec(all[i]);
     return VX_OK;
 }
 
@@ -363,7 +373,15 @@ extern "C" int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, voi
 
 extern "C" int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layout,
                               const vx_trace_opts* opts, void* stream) {
+    return vx_trace_batch_timed(items, count, hit_layout, opts, stream, nullptr, 0, nullptr);
+}
+
+extern "C" int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit_layout,
+                                    const vx_trace_opts* opts, void* stream, void** events, uint32_t n_events,
+                                    uint32_t* groups) {
     clear_error();
+    if (groups) *groups = 0;
+    if (n_events > 0 && !events) return fail(VX_EINVAL, "events is NULL");
     if (count == 0) return VX_OK;
     if (!items) return fail(VX_EINVAL, "items is NULL");
     if (count > 65536) return fail(VX_EINVAL, "at most 65536 items per batch");
@@ -387,7 +405,7 @@ extern "C" int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_
     if (in.empty()) return VX_OK;
     DeviceScope ds(dev);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
-    return launch_batch(in, hit_layout, opts, stream);
+    return launch_batch(in, hit_layout, opts, stream, events, n_events, groups);
 }
 
 // ---------------------------------------------------------------------------

@@ -119,6 +119,10 @@ const KernelSet* find_kernels(const std::string& spec) {
 
 const KernelSet* generic_kernels() { return &g_generic; }
 
+std::vector<const KernelSet*> registered_kernel_sets() { return registry(); }
+
+const char* kernel_set_spec(const KernelSet* k) { return k->spec; }
+
 bool kernel_set_specialized(const KernelSet* k) { return k && k->specialized; }
 
 static bool same_params(const FmtParams& a, const FmtParams& b) { return memcmp(&a, &b, sizeof(FmtParams)) == 0; }
@@ -232,12 +236,16 @@ std::mutex g_fork_mu;
 DevStreams g_fork[64];
 }  // namespace
 
-int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream) {
+int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream,
+                 void** events, uint32_t n_events, uint32_t* groups) {
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce) return fail(VX_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
     if (dev >= 64) return fail(VX_EUNSUPPORTED, "device %d", dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce || sms < 1) return fail(VX_ECUDA, "SM count: %s", cudaGetErrorString(ce));
+    if (groups) *groups = 0;
     // group by (kernel set, format parameters)
     struct Sub {
         const KernelSet* ks;
@@ -294,33 +302,63 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (e) return fail(VX_ECUDA, "batch events: %s", cudaGetErrorString(e));
         F.ready = true;
     }
-    cudaError_t e = cudaEventRecord(F.fork, st);
-    if (e) return fail(VX_ECUDA, "batch fork: %s", cudaGetErrorString(e));
     const int nsub = (int)subs.size();
-    for (int i = 0; i < nsub && i < kForkStreams; i++) cudaStreamWaitEvent(F.s[i], F.fork, 0);
+    // Grid of every group, decided before anything is enqueued: a failure
+    // here leaves no forked stream behind.
+    // Every launch gets a full GPU's worth of resident blocks: the launches
+    // run one after another in effect, each draining its queue with all SMs,
+    // and the next one's blocks start as the previous one's retire (separate
+    // streams), so no SM waits for a slower group.
+    std::vector<int> grids(nsub);
     for (int i = 0; i < nsub; i++) {
-        Sub& g = subs[i];
+        const Sub& g = subs[i];
         int per_sm = 1;
         int rc = g.ks->resident_blocks(g.v0->spec.fmt, layout, block, &per_sm);
         if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
-        // Every launch gets a full GPU's worth of resident blocks: the
-        // launches run one after another in effect, each draining its queue
-        // with all SMs, and the next one's blocks start as the previous one's
-        // retire (separate streams), so no SM waits for a slower group.
         const uint64_t n = g.d.start[g.d.count];
         uint64_t grid = (uint64_t)sms * per_sm;
         const uint64_t need = (n + block - 1) / block;
         if (grid > need) grid = need;
-        if (grid < 1) grid = 1;
+        grids[i] = grid < 1 ? 1 : (int)grid;
+    }
+    cudaError_t e = cudaEventRecord(F.fork, st);
+    if (e) return fail(VX_ECUDA, "batch fork: %s", cudaGetErrorString(e));
+    const int nfork = nsub < kForkStreams ? nsub : kForkStreams;
+    int forked = 0;
+    for (; forked < nfork; forked++) {
+        e = cudaStreamWaitEvent(F.s[forked], F.fork, 0);
+        if (e) break;
+    }
+    int rc = e ? fail(VX_ECUDA, "batch fork: %s", cudaGetErrorString(e)) : VX_OK;
+    for (int i = 0; i < nsub && !rc; i++) {
+        Sub& g = subs[i];
+        cudaStream_t fs = F.s[i % kForkStreams];
+        const bool timed = events && (uint32_t)(2 * i + 1) < n_events;
+        if (timed && (e = cudaEventRecord((cudaEvent_t)events[2 * i], fs))) {
+            rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
+            break;
+        }
         unsigned long long* next = g.v0->queue_counter();
-        rc = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, (int)grid, refill, burst, F.s[i % kForkStreams],
-                               next);
-        if (rc) return fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)rc));
+        int lr = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, grids[i], refill, burst, fs, next);
+        if (lr) {
+            rc = fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)lr));
+            break;
+        }
+        if (timed && (e = cudaEventRecord((cudaEvent_t)events[2 * i + 1], fs))) {
+            rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (groups) *groups = (uint32_t)(i + 1);
     }
-    for (int i = 0; i < nsub && i < kForkStreams; i++) {
-        cudaEventRecord(F.join[i], F.s[i]);
-        cudaStreamWaitEvent(st, F.join[i], 0);
+    // Join every forked stream back into the caller's stream, on success and
+    // on failure alike: a stream left forked would invalidate a capture in
+    // progress and keep waiting on the caller's work.
+    for (int i = 0; i < forked; i++) {
+        cudaError_t j1 = cudaEventRecord(F.join[i], F.s[i]);
+        cudaError_t j2 = j1 ? j1 : cudaStreamWaitEvent(st, F.join[i], 0);
+        if (j2 && !rc) rc = fail(VX_ECUDA, "batch join: %s", cudaGetErrorString(j2));
     }
+    if (rc) return rc;
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "batch: %s", cudaGetErrorString(e));
     return VX_OK;

@@ -60,9 +60,7 @@ __global__ void __launch_bounds__(256) k_trace_noalloc(DynF f, const Img pool,
                                                        int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint2 stack[DynF::kMaxJ + 2];  // node stack + start voxel
-    Walker<false, DynF> w;
-    w.S = stack;
+    Walker<false, DynF> w;  // node stack in the kernel's dynamic shared memory
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint32_t idx = 0;
@@ -120,10 +118,12 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     int rc = scratch_address(dev, &next);
     if (rc) return rc;
     int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e || sms < 1) return fail(VX_ECUDA, "SM count query: %s", cudaGetErrorString(e));
     const int block = 256;
-    e = layout == VX_HIT_FULL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<0>, block, 0)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<1>, block, 0);
+    const size_t sm = stack_bytes(V.spec.fmt.J, block);
+    e = layout == VX_HIT_FULL ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<0>, block, sm)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_noalloc<1>, block, sm);
     if (e) return fail(VX_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = (uint64_t)sms * per_sm;
@@ -135,10 +135,10 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     DynF f;
     f.p = V.spec.fmt;
     if (layout == VX_HIT_FULL)
-        k_trace_noalloc<0><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<0><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     else
-        k_trace_noalloc<1><<<(unsigned)grid, block, 0, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<1><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "vx_trace_noalloc launch: %s", cudaGetErrorString(e));

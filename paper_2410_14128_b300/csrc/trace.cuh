@@ -285,8 +285,8 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // without leaving the loop (persistent kernels).
 //
 // The node stack (pointer and valid mask of the node entered at each node
-// level, one 8-byte entry per level) is an array of the calling kernel,
-// passed in as a pointer so that the walker's scalars stay in registers.
+// level, one 8-byte entry per level, and the start voxel) lives in the
+// kernel's dynamic shared memory (vx_dyn_smem below), one column per thread.
 //
 // RESTART selects the paper's restarting sparse-voxel intersection (Sec.
 // 4.4): only the root node of each format level is kept; leaving a node of
@@ -294,9 +294,22 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // to the resuming node level, at the price of re-reading those nodes.
 //
 // TOPS: the cells of node level 0 (a Raw or DF top level) were copied into
-// vx_top_smem by the calling kernel, and level-0 look-ups read them there.
-extern __shared__ uint32_t vx_top_smem[];
+// shared memory by the calling kernel (after the node stacks), and level-0
+// look-ups read them there.
+//
+// Dynamic shared memory of every walker kernel: first the node stacks of the
+// block's threads, entry e of thread t at vx_dyn_smem[e * blockDim.x + t]
+// (stack_entries(J) entries of 8 bytes per thread), then, in a persistent
+// kernel that stages the top level, its words.  Lanes of a warp touch
+// consecutive 8-byte entries whatever entry each reads, so the accesses are
+// free of bank conflicts, and the stack takes no L1 lines from node reads.
+extern __shared__ __align__(16) uint2 vx_dyn_smem[];
 constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB: R(4,4,4) or D(4,4,4,M)
+
+// Entries per thread: one {pointer, valid mask} per node level, then two
+// holding the ray's start voxel.
+__host__ __device__ constexpr uint32_t stack_entries(uint32_t J) { return J + 2u; }
+inline size_t stack_bytes(uint32_t J, int block) { return (size_t)stack_entries(J) * (size_t)block * sizeof(uint2); }
 
 template <bool COUNT, class F, bool RESTART = false, bool TOPS = false>
 struct Walker {
@@ -311,7 +324,6 @@ struct Walker {
     int skip;  // DF level: cells the walk may still enter without a look-up
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
-    uint2* S;         // owned by the caller: F::kMaxJ node-stack entries, then 2 holding the start voxel
     uint32_t lim;     // words in the image (checked by the instrumented walker)
     uint32_t* sect;   // instrumented walker: one bit per 32-byte sector of the image it read, or null
     Cnt cnt;
@@ -331,6 +343,24 @@ struct Walker {
         return ldw(pool, i);
     }
 
+
+    // Node-stack entry e of this thread (0 <= e < stack_entries(J); entries
+    // J and J + 1 hold the start voxel).  Every index the walk forms lies in
+    // that range by construction (j only grows by descents below J - 1 and
+    // pops to jpop(h) <= j); the instrumented walker also checks it and
+    // refuses an access outside it (counted like a refused read).
+    __device__ __forceinline__ int sidx(const F& f, int e) {
+        if (COUNT && (unsigned)e >= stack_entries((uint32_t)f.J())) {
+            cnt.refused++;
+            e = 0;
+        }
+        return e * (int)blockDim.x + (int)threadIdx.x;
+    }
+    __device__ __forceinline__ uint2 sget(const F& f, int e) { return vx_dyn_smem[sidx(f, e)]; }
+    __device__ __forceinline__ void sput(const F& f, int e, uint2 v) { vx_dyn_smem[sidx(f, e)] = v; }
+    __device__ __forceinline__ const uint32_t* top_words_smem(const F& f) const {
+        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_entries((uint32_t)f.J()) * blockDim.x);
+    }
 
     // Node level j: kind, children side (log2 voxels), fanout per axis, and
     // whether its children are terminating integers -- extracted from the
@@ -353,7 +383,7 @@ struct Walker {
     __device__ __forceinline__ void restart(const F& f, const Img im) {
         const uint32_t* __restrict__ pool = im.w;
         const int r = 31 - __clz(f.top() & ((2u << j) - 1u));
-        const uint2 e = S[r];
+        const uint2 e = sget(f, r);
         uint32_t p = e.x, m = e.y;
         const bool svo = f.has_svo() && f.kind(r) == K_SVO;
         const int sj = f.s(j);
@@ -469,10 +499,11 @@ struct Walker {
             }
             v0l[i] = min(max(v, 0), n - 1);
         }
-        // the start voxel is read only by descents before the first step:
-        // it lives in the stack array's two extra entries, not in registers
-        S[F::kMaxJ] = make_uint2((uint32_t)v0l[0], (uint32_t)v0l[1]);
-        S[F::kMaxJ + 1] = make_uint2((uint32_t)v0l[2], 0u);
+        // the start voxel is read only by descents before the first step and
+        // by the FP64 tie rule: it lives in the stack's two extra entries,
+        // not in registers
+        sput(f, f.J(), make_uint2((uint32_t)v0l[0], (uint32_t)v0l[1]));
+        sput(f, f.J() + 1, make_uint2((uint32_t)v0l[2], 0u));
 
         // ---- root node ----
         const uint32_t root = rd(pool, 0);
@@ -489,7 +520,7 @@ struct Walker {
             else { Pc = root; Mc = rd(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
         }
         j = 0;
-        S[0] = make_uint2(Pc, Mc);
+        sput(f, 0, make_uint2(Pc, Mc));
         {
             const int s0 = f.s(0);
 #pragma unroll
@@ -583,7 +614,7 @@ struct Walker {
             if (RESTART) {
                 restart(f, im);
             } else {
-                const uint2 e = S[j];
+                const uint2 e = sget(f, j);
                 Pc = e.x;
                 Mc = e.y;
             }
@@ -622,8 +653,8 @@ struct Walker {
         const uint32_t as = is_df ? 2u * idx : idx;  // word of the cell in a staged top level
         const bool staged = TOPS && j == 0;
         uint32_t w = 0, dist = 0;
-        if (is_raw || df_read) w = staged ? vx_top_smem[as] : rd(pool, a);
-        if (df_read) dist = staged ? vx_top_smem[as + 1] : rd(pool, a + 1);  // same sector as the cell word
+        if (is_raw || df_read) w = staged ? top_words_smem(f)[as] : rd(pool, a);
+        if (df_read) dist = staged ? top_words_smem(f)[as + 1] : rd(pool, a + 1);  // same sector as the cell word
         VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
         const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;
         if (is_df) skip = df_read ? (occ ? 0 : (int)dist - 1) : skip - 1;
@@ -666,13 +697,13 @@ struct Walker {
                 else { Pn = term; Mn = rd(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
-            if (!RESTART || ((f.top() >> j) & 1u)) S[j] = make_uint2(Pn, Mn);
+            if (!RESTART || ((f.top() >> j) & 1u)) sput(f, j, make_uint2(Pn, Mn));
             Pc = Pn;
             Mc = Mn;
             const int sn = ls(f), bn = lb(f, 0);
             const float scale = __int_as_float((127 - sn) << 23);  // 2^-sn
             if (fresh) {  // no step yet: the cell holding the start voxel
-                const uint2 a01 = S[F::kMaxJ], a2 = S[F::kMaxJ + 1];
+                const uint2 a01 = sget(f, J), a2 = sget(f, J + 1);
                 c[0] = (int)a01.x >> sn;
                 c[1] = (int)a01.y >> sn;
                 c[2] = (int)a2.x >> sn;
@@ -696,7 +727,7 @@ struct Walker {
                     // a ray that started on plane B took the start voxel's
                     // convention; a crossing at that same instant must not undo it
                     // (away from the band the cell is past the start anyway)
-                    const uint2 sv = i == 2 ? S[F::kMaxJ + 1] : S[F::kMaxJ];
+                    const uint2 sv = sget(f, i == 2 ? J + 1 : J);
                     const int vs = (int)(i == 1 ? sv.y : sv.x) >> sn;
                     cn = sgn(i) > 0 ? max(cn, vs) : min(cn, vs);
                 }
@@ -714,9 +745,7 @@ struct Walker {
 template <bool COUNT, class F, bool RESTART = false>
 __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt,
                                             uint32_t* sect = nullptr) {
-    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
-    Walker<COUNT, F, RESTART> w;
-    w.S = stack;
+    Walker<COUNT, F, RESTART> w;  // node stack in the kernel's dynamic shared memory
     w.sect = sect;
     HitRec h;
     if (!w.start(f, pool, r, h))
@@ -844,9 +873,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
                                                            unsigned long long* next, int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
-    Walker<false, F> w;
-    w.S = stack;
+    Walker<false, F> w;  // node stack in the kernel's dynamic shared memory
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t slot = 0;
@@ -894,8 +921,9 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // `next` must be zero at launch; the kernel leaves it >= n.
 //
 // TS: the block first copies the top level's `top_words` words (a Raw or DF
-// level 0, at most kTopSmemMaxWords) into shared memory; the launch provides
-// 4 top_words bytes of dynamic shared memory.
+// level 0, at most kTopSmemMaxWords) into shared memory, after the node
+// stacks; the launch provides stack_bytes(J, block) + 4 top_words bytes of
+// dynamic shared memory.
 template <class F, int LAYOUT, bool RS = false, bool TS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
@@ -905,14 +933,13 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (TS) {
+        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_entries((uint32_t)f.J()) * blockDim.x);
         const uint32_t root = ldw(pool.w, 0);
         if (root != 0)
-            for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) vx_top_smem[i] = ldw(pool.w, root + i);
+            for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) top[i] = ldw(pool.w, root + i);
         __syncthreads();
     }
-    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
-    Walker<false, F, RS, TS> w;
-    w.S = stack;
+    Walker<false, F, RS, TS> w;  // node stack in the kernel's dynamic shared memory
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -970,9 +997,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint64_t n = desc.start[desc.count];
-    uint2 stack[F::kMaxJ + 2];  // node stack + start voxel
-    Walker<false, F> w;
-    w.S = stack;
+    Walker<false, F> w;  // node stack in the kernel's dynamic shared memory
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -1081,10 +1106,11 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
-        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
-        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
-        else k_trace<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, order, n, hits);
+        const size_t sm = stack_bytes(p.J, block);
+        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        else k_trace<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
         return (int)cudaGetLastError();
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
@@ -1093,14 +1119,15 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
+        const size_t sm = stack_bytes(p.J, block);
         if (layout == 0 && !restart)
-            k_trace_count<F, 0, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
+            k_trace_count<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters, sectors);
         else if (layout == 0)
-            k_trace_count<F, 0, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
+            k_trace_count<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters, sectors);
         else if (!restart)
-            k_trace_count<F, 1, false><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
+            k_trace_count<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters, sectors);
         else
-            k_trace_count<F, 1, true><<<(unsigned)grid, block, 0, st>>>(f, pool, rays, n, hits, counters, sectors);
+            k_trace_count<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters, sectors);
         return (int)cudaGetLastError();
     }
     // Words of a Raw / DF top level that fits the shared-memory staging, else 0.
@@ -1112,25 +1139,34 @@ struct Launch {
         return words <= kTopSmemMaxWords ? (uint32_t)words : 0u;
     }
     template <bool RS, bool TS>
-    static int persistent_as(const F& f, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
-                             void* hits, int layout, int block, int per_sm_req, int refill, int burst,
+    static int persistent_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
+                             uint64_t n, void* hits, int layout, int block, int per_sm_req, int refill, int burst,
                              cudaStream_t st, unsigned long long* next, uint32_t tw) {
+        const F f = make(p);
         int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t smem = TS ? (size_t)tw * sizeof(uint32_t) : 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e) return (int)e;
+        const size_t smem = stack_bytes(p.J, block) + (TS ? (size_t)tw * sizeof(uint32_t) : 0);
+        if (TS && smem > 48 * 1024) {  // above the default limit of dynamic shared memory
+            e = layout == 0 ? cudaFuncSetAttribute(k_trace_persistent<F, 0, RS, TS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_trace_persistent<F, 1, RS, TS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return (int)e;
+        }
         int per_sm = per_sm_req;
         if (per_sm <= 0) {
-            cudaError_t e = layout == 0
-                                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, RS, TS>, block, smem)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, RS, TS>, block, smem);
+            e = layout == 0
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, RS, TS>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, RS, TS>, block, smem);
             if (e) return (int)e;
             if (per_sm < 1) per_sm = 1;
         }
         uint64_t grid = (uint64_t)sms * per_sm;
         const uint64_t need = (n + (uint64_t)block - 1) / (uint64_t)block;
         if (grid > need) grid = need;
-        cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+        e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         const unsigned g = (unsigned)grid;
         if (layout == 0)
@@ -1146,31 +1182,32 @@ struct Launch {
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
                                 int burst, int restart, int smem_top, cudaStream_t st, unsigned long long* next) {
         if (n == 0) return 0;
-        const F f = make(p);
         const uint32_t tw = top_words(p);
         if (restart)
-            return persistent_as<true, false>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+            return persistent_as<true, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                               burst, st, next, 0);
         if (smem_top && tw)
-            return persistent_as<false, true>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+            return persistent_as<false, true>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                               burst, st, next, tw);
-        return persistent_as<false, false>(f, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+        return persistent_as<false, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0);
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
+        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, 0);
+                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, sm)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, sm);
         if (*per_sm < 1) *per_sm = 1;
         return (int)e;
     }
     static int trace_batch(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill,
                            int burst, cudaStream_t st, unsigned long long* next) {
         const F f = make(p);
+        const size_t sm = stack_bytes(p.J, block);
         cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
-        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
-        else k_trace_batch<F, 1><<<(unsigned)grid, block, 0, st>>>(f, d, next, refill, burst);
+        if (layout == 0) k_trace_batch<F, 0><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
+        else k_trace_batch<F, 1><<<(unsigned)grid, block, sm, st>>>(f, d, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render_persistent(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -1179,11 +1216,12 @@ struct Launch {
         if (n == 0) return 0;
         const F f = make(p);
         int dev = 0, sms = 0, per_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = layout == 0
-                            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, 0);
+        const size_t sm = stack_bytes(p.J, block);
+        cudaError_t e = cudaGetDevice(&dev);
+        if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e) return (int)e;
+        e = layout == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 0>, block, sm)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, sm);
         if (e) return (int)e;
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)sms * per_sm;
@@ -1192,9 +1230,9 @@ struct Launch {
         e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         if (layout == 0)
-            k_render_persistent<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         else
-            k_render_persistent<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
@@ -1207,10 +1245,11 @@ struct Launch {
         const uint64_t threads = tiles_w * tile_rows * 32u;
         const uint64_t grid = (threads + (uint64_t)block - 1) / (uint64_t)block;
         if (grid > 0x7FFFFFFFull) return (int)cudaErrorInvalidConfiguration;
+        const size_t sm = stack_bytes(p.J, block);
         if (layout == 0)
-            k_render<F, 0><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
+            k_render<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
         else
-            k_render<F, 1><<<(unsigned)grid, block, 0, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
+            k_render<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
         return (int)cudaGetLastError();
     }
 };

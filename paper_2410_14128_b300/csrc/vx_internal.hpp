@@ -153,6 +153,8 @@ bool kernel_set_specialized(const KernelSet* k);
 // the run-time-described kernels for any other signature.
 const KernelSet* find_kernels(const std::string& canonical_spec);
 const KernelSet* generic_kernels();
+std::vector<const KernelSet*> registered_kernel_sets();  // compile-time-composed sets, in registration order
+const char* kernel_set_spec(const KernelSet* k);
 
 int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, const vx_trace_opts* o,
                  void* stream);
@@ -169,7 +171,10 @@ struct BatchItemIn {
     uint64_t n;
     void* hits;
 };
-int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream);
+// events: optional, n_events caller-created events recorded around group k's
+// kernel (2k before, 2k + 1 after) on its stream; *groups receives the count.
+int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream,
+                 void** events = nullptr, uint32_t n_events = 0, uint32_t* groups = nullptr);
 uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbins_out);
 int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* scratch, uint32_t** order_out,
               struct CUstream_st* st);

@@ -112,6 +112,10 @@ class Result:
     done: float
     refused: str | None = None
     digest: tuple | None = None
+    epoch: int = 0                        # launch epoch of the server (0: not launched)
+    stream: int = -1                      # index of the server stream that carried it
+    device_start_ms: float | None = None  # with record_device_times: the request's device work,
+    device_end_ms: float | None = None    # ms after the server's start event (CUDA events)
 
     @property
     def latency(self) -> float:
@@ -121,7 +125,11 @@ class Result:
 class Server:
     def __init__(self, volumes: dict, mem_budget_bytes: int, max_inflight: int = 256, streams: int = 4,
                  layout: int = HIT_FULL, clock=time.perf_counter, keep_hits: bool = True, digest_every: int = 1,
-                 host_arena: HostArena | None = None):
+                 host_arena: HostArena | None = None, record_device_times: bool = False):
+        """record_device_times: bracket each request's device work (copies,
+        kernels, download) with timing CUDA events on its stream and report
+        the interval in Result.device_start_ms / device_end_ms, so that
+        overlap between requests can be read from the GPU's own clock."""
         import torch
         self.torch = torch
         self.volumes = volumes
@@ -134,7 +142,8 @@ class Server:
         self.clock = clock
         self.t0 = clock()
         self.pending: deque = deque()
-        # per stream, in launch order: (req, admitted_time, bytes, event, host_buffer, keep)
+        # per stream, in launch order: (req, admitted_time, bytes, completion event, host_buffer, keep,
+        # epoch, start event or None, stream index)
         self.inflight = [deque() for _ in self.streams]
         self.n_inflight = 0
         # pinned download space, as large as the device budget by default
@@ -143,6 +152,9 @@ class Server:
         self.epochs = 0
         self.keep_hits = keep_hits  # else keep only a digest of each result
         self.digest_every = max(1, digest_every)  # digest request ids divisible by this
+        self.max_inflight_seen = 0  # most requests on the GPU at once
+        self.record_device_times = record_device_times
+        self.base_event = None
 
     def now(self) -> float:
         return self.clock() - self.t0
@@ -225,17 +237,25 @@ class Server:
         self.next_stream = (self.next_stream + 1) % len(self.streams)
         return k, self.streams[k]
 
-    def _finish(self, req, now, need, slot, hits, keep, k, stream):
+    def _start_event(self, stream):
+        if not self.record_device_times:
+            return None
+        ev = self.torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        return ev
+
+    def _finish(self, req, now, need, slot, hits, keep, k, stream, start_ev=None):
         # download on the request's stream into its slot of the pinned arena;
         # the event marks completion
         torch = self.torch
         nbytes = hits.numel() * hits.element_size()
         buf = self.arena.view(slot[0], nbytes)
         buf.view(hits.dtype).view(hits.shape).copy_(hits, non_blocking=True)
-        ev = torch.cuda.Event()
+        ev = torch.cuda.Event(enable_timing=self.record_device_times)
         ev.record(stream)
-        self.inflight[k].append((req, now, need, ev, (slot, buf), keep))
+        self.inflight[k].append((req, now, need, ev, (slot, buf), keep, self.epochs, start_ev, k))
         self.n_inflight += 1
+        self.max_inflight_seen = max(self.max_inflight_seen, self.n_inflight)
 
     def _launch(self, admitted, now):
         torch = self.torch
@@ -249,15 +269,17 @@ class Server:
             k, stream = self._stream()
             with torch.cuda.stream(stream):
                 hits = alloc_hits(req.n, self.layout)
+                start_ev = self._start_event(stream)
                 try:
                     vol.render(req.camera, hits, self.layout, stream=stream)
                 except VxError as e:  # rejected before anything was enqueued
                     self._refuse(req, now, need, slot, f"rejected: {e}")
                     continue
-                self._finish(req, now, need, slot, hits, [hits], k, stream)
+                self._finish(req, now, need, slot, hits, [hits], k, stream, start_ev)
         if traces:
             k, stream = self._stream()
             with torch.cuda.stream(stream):
+                start_ev = self._start_event(stream)
                 batch, launched = [], []
                 for req, need, slot, vol in traces:
                     hits = alloc_hits(req.n, self.layout)
@@ -271,7 +293,7 @@ class Server:
                         self._refuse(req, now, need, slot, f"rejected: {e}")
                     return
                 for req, need, slot, hits, keep in launched:
-                    self._finish(req, now, need, slot, hits, keep, k, stream)
+                    self._finish(req, now, need, slot, hits, keep, k, stream, start_ev)
 
     def _poll(self) -> int:
         # work on one stream completes in launch order: look at each stream's
@@ -279,14 +301,16 @@ class Server:
         done = 0
         for q in self.inflight:
             while q and q[0][3].query():
-                req, adm, need, ev, (slot, buf), keep = q.popleft()
+                req, adm, need, ev, (slot, buf), keep, epoch, start_ev, k = q.popleft()
                 t = self.now()
                 h = buf.numpy().view(hit_dtype(self.layout)).reshape(-1)
                 dg = digest(h) if req.id % self.digest_every == 0 else None
-                if self.keep_hits:
-                    self.results[req.id] = Result(req.id, h.copy(), req.arrival, adm, t, digest=dg)
-                else:
-                    self.results[req.id] = Result(req.id, None, req.arrival, adm, t, digest=dg)
+                res = Result(req.id, h.copy() if self.keep_hits else None, req.arrival, adm, t, digest=dg,
+                             epoch=epoch, stream=k)
+                if start_ev is not None:
+                    res.device_start_ms = self.base_event.elapsed_time(start_ev)
+                    res.device_end_ms = self.base_event.elapsed_time(ev)
+                self.results[req.id] = res
                 self.arena.release(*slot)
                 self.used -= need
                 self.n_inflight -= 1
@@ -301,6 +325,9 @@ class Server:
         if not realtime:
             for r in reqs:
                 r.arrival = 0.0
+        if self.record_device_times:
+            self.base_event = self.torch.cuda.Event(enable_timing=True)
+            self.base_event.record()
         self.t0 = self.clock()
         i = 0
         total = len(reqs)

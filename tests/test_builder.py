@@ -64,13 +64,35 @@ def test_struct_layouts_match_header(tmp_path):
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "vx.h"\n'
                    'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(vx_stats), '
                    'offsetof(vx_stats, upload_ms), offsetof(vx_stats, tuned), offsetof(vx_stats, tuned_opts), '
-                   'sizeof(vx_trace_opts), sizeof(vx_batch_item)); return 0; }\n')
+                   'sizeof(vx_trace_opts), sizeof(vx_batch_item)); '
+                   'printf("%zu %zu\\n", sizeof(vx_build_opts), offsetof(vx_build_opts, generic_kernel)); '
+                   'return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(vx._Stats), vx._Stats.upload_ms.offset, vx._Stats.tuned.offset,
-            vx._Stats.tuned_opts.offset, ctypes.sizeof(vx._TraceOpts), ctypes.sizeof(vx._BatchItem)]
+            vx._Stats.tuned_opts.offset, ctypes.sizeof(vx._TraceOpts), ctypes.sizeof(vx._BatchItem),
+            ctypes.sizeof(vx._BuildOpts), vx._BuildOpts.generic_kernel.offset]
     assert got == want
+
+
+def test_compiled_formats_are_the_instantiated_ones():
+    # vx_formats lists every format composed at compile time, once, in the
+    # spelling of its instantiation
+    import glob
+    text = "".join(open(f).read() for f in glob.glob(os.path.join(ROOT, "paper_2410_14128_b300", "csrc",
+                                                                  "formats_*.cu")))
+    listed = re.findall(r'^VX_FMT\(\w+, "([^"]+)"', text, flags=re.M)
+    specs = vx.compiled_formats()
+    assert len(specs) == len(set(specs)) == len(listed) >= 44
+    assert sorted(specs) == sorted(listed)
+
+
+def test_generic_kernel_option_selects_the_run_time_kernels():
+    g = synth.value_noise_volume(101, 64)
+    assert build("S(4) R(2,2,2)", g).stats()["specialized"]
+    assert not build("S(4) R(2,2,2)", g, generic_kernel=True).stats()["specialized"]
+    assert not build("S(2) R(4,4,4)", g).stats()["specialized"]  # not compiled in
 
 
 def test_stats_report_no_tuning_before_autotune():

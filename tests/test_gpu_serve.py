@@ -79,6 +79,30 @@ def test_results_same_alone_and_in_the_mix(volumes):
     assert st["p99_ms"] >= st["p50_ms"] > 0
 
 
+def test_requests_are_admitted_while_others_run_and_overlap_on_the_gpu(volumes):
+    # continuous batching: a request that arrives while others are on the GPU
+    # is admitted as soon as memory allows, and its device work overlaps
+    # theirs (read from CUDA events on the server's streams)
+    vols, grids = volumes
+    reqs = make_requests(15, 80, 0.03, grids)
+    srv = serve.Server(vols, mem_budget_bytes=8 << 20, record_device_times=True)
+    res = srv.run(reqs, realtime=True)
+    for r in reqs:
+        out = res[r.id]
+        assert out.refused is None
+        assert np.array_equal(out.hits, alone(vols, r)), r.id
+        assert out.device_end_ms >= out.device_start_ms >= 0.0
+    done = sorted(res.values(), key=lambda r: r.admitted)
+    admitted_in_flight = [(a.id, b.id) for a in done for b in done
+                          if b.epoch > a.epoch and a.admitted <= b.admitted < a.done]
+    assert admitted_in_flight, "no request was admitted while an earlier one was in flight"
+    assert srv.max_inflight_seen >= 2
+    overlapping = [(a.id, b.id) for a in done for b in done
+                   if a.stream != b.stream and a.id < b.id
+                   and a.device_start_ms < b.device_end_ms and b.device_start_ms < a.device_end_ms]
+    assert overlapping, "no two requests on different streams overlapped on the GPU"
+
+
 def test_memory_admission_defers_and_refuses(volumes):
     vols, grids = volumes
     reqs = make_requests(12, 20, 0.0, grids)
