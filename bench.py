@@ -307,14 +307,16 @@ def _scene2048():
     return _SCENE
 
 
-def batch_recipe():
+def batch_recipe(scale: float = 1.0):
     """The 64 ray sets of the batched workload: (k, size, kind, parameter)
     with kind "view" (a camera of about `size` pixels, 16:9) or
     "incoherent" (synth.incoherent_rays seed); set k belongs to
-    BATCH_FORMATS[k % 4]."""
+    BATCH_FORMATS[k % 4].  scale < 1 shrinks every set (a small case of the
+    same workload, for profiler captures)."""
     import synth
     rng = np.random.default_rng(SEED3 + 4)
-    sizes = np.exp(rng.uniform(np.log(65536), np.log(8388608), N_SETS)).astype(np.int64)
+    sizes = np.exp(rng.uniform(np.log(65536), np.log(8388608), N_SETS))
+    sizes = np.maximum(1024, sizes * scale).astype(np.int64)
     out = []
     for k, n in enumerate(sizes):
         if k % 2 == 0:
@@ -438,7 +440,7 @@ def run_headline(args):
 
     sc, g8 = _scene2048()
     vols = [vx.Volume(s, g8, palette=sc.palette) for s in BATCH_FORMATS]
-    recipe = batch_recipe()
+    recipe = batch_recipe(args.batch_scale)
     rays = batch_rays_device(vx, torch, recipe)
     sets = [(vols[k % len(vols)], rays[k], vx.alloc_hits(rays[k].shape[0])) for k in range(N_SETS)]
     total = sum(r.shape[0] for r in rays)
@@ -451,7 +453,7 @@ def run_headline(args):
             tuned.append(v.autotune(own))
 
     # --- algorithmic bytes per ray and footprint (instrumented kernel, outside timing) ---
-    node_bytes = []
+    node_bytes, iters = [], []
     sects = [v.alloc_sectors() for v in vols]
     for k, (v, r, _) in enumerate(sets):
         c = torch.zeros(4, dtype=torch.int64, device="cuda")
@@ -459,6 +461,7 @@ def run_headline(args):
         v.trace_counted(r, tmp, c, sectors=sects[k % len(vols)])
         torch.cuda.synchronize()
         node_bytes.append(int(c[0]))
+        iters.append(int(c[1]))
         del tmp
     footprint = [vx.Volume.footprint_bytes(s) for s in sects]
     del sects
@@ -629,6 +632,10 @@ def run_headline(args):
                               "sets": len(own), "rays": int(sum(rays[k].shape[0] for k in own)),
                               "node_bytes_per_ray": round(sum(node_bytes[k] for k in own) /
                                                           sum(rays[k].shape[0] for k in own), 2),
+                              "iters_per_ray": round(sum(iters[k] for k in own) /
+                                                     sum(rays[k].shape[0] for k in own), 2),
+                              "ray_kind": "camera views" if i % 2 == 0 else "incoherent",
+                              "footprint_bytes": footprint[i],
                               "kernel_ms": round(float(np.mean(group_ms[i])), 4),
                               "specialized_kernel": st["specialized"]})
     for v in vols:
@@ -651,7 +658,9 @@ def run_headline(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "formats": BATCH_FORMATS, "rays_per_step": total, "sets": N_SETS,
+            "config": {"workload": WORKLOAD + (f" (sets scaled by {args.batch_scale:g})" if args.batch_scale != 1.0
+                                               else ""),
+                       "formats": BATCH_FORMATS, "rays_per_step": total, "sets": N_SETS,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2: {32 * total / 1e9:.2f} GB of rays and {16 * total / 1e9:.2f} GB "
                              f"of hits per step (L2 126 MB)",
@@ -1341,6 +1350,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-512", action="store_true")
     ap.add_argument("--steps512", type=int, default=100)
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="shrink the 64 batched sets (a small case for profiler captures; the line says so)")
     ap.add_argument("--sweep-steps", type=int, default=3)
     ap.add_argument("--sweep-fast", action="store_true", help="skip the stack vs restart columns of the sweep")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

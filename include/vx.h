@@ -130,13 +130,19 @@ typedef struct vx_grid {
  *   no_upload     1 = build on the host only (vx_trace then fails);
  *   threads       host threads for the build, 0 = all cores;
  *   canonical_device  1 = put the canonical words on the device as they
- *                 are; 0 (default) = use the packed device layout when the
- *                 volume is below 2^24 words: same offsets, but each pointer
- *                 to an SVDAG node carries the node's valid mask in bits
- *                 24..31 and an SVDAG slot of a leaf child holds the leaf's
- *                 terminating integer, which saves one or two dependent reads
- *                 per SVDAG level (vx_canonical always returns the paper's
- *                 layout);
+ *                 are; 0 (default) = a device image with the same structures
+ *                 in the same order, relocated so that every DF cell array,
+ *                 SVO root entry and SVO child list starts at an even word
+ *                 (a DF cell {terminating integer, distance} and an SVO node
+ *                 entry {pointer, masks} are then one 8-byte load; one zero
+ *                 word of padding where needed), and, when the format has an
+ *                 SVDAG level and the image stays below 2^24 words, packed:
+ *                 each pointer to an SVDAG node carries the node's valid mask
+ *                 in bits 24..31 and an SVDAG slot of a leaf child holds the
+ *                 leaf's terminating integer (the leaf words are dropped),
+ *                 which saves one or two dependent reads per SVDAG level.
+ *                 vx_canonical always returns the paper's layout; vx_stats
+ *                 reports the device image's size and which changes apply;
  *   generic_kernel  1 = trace with the kernels that take the format as a
  *                 run-time argument even when a compile-time-composed kernel
  *                 exists for the spec (same results; for checking the two
@@ -238,8 +244,14 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *          per octree depth, redundant node reads).  Used by vx_trace and
  *          vx_trace_counted; vx_render, vx_trace_batch and vx_trace_noalloc
  *          always keep the stack.  Any other value: VX_EINVAL.
- * Persistent launches take a queue counter from a ring of 256 per volume, so
- * up to 256 of them may be in flight at once per volume. */
+ * Persistent launches (and the kernels of vx_trace_batch) each need a
+ * ray-queue counter of the volume.  A launch issued directly takes one from a
+ * ring of 256 per volume, so at most 256 of them may be in flight at once per
+ * volume.  A launch captured into a CUDA graph gets a counter of its own,
+ * which every replay of that graph reuses and no other launch ever takes; a
+ * volume has 3840 of those, and a capture beyond them fails with
+ * VX_EUNSUPPORTED.  Replays of one graph must therefore not overlap each
+ * other (replay it on one stream). */
 typedef struct vx_trace_opts {
     int32_t mode;
     int32_t block;
@@ -261,7 +273,7 @@ typedef struct vx_stats {
     uint32_t log2_dim[3];
     int32_t specialized;     /* 1 = a compile-time-composed kernel serves this spec */
     int32_t packed;          /* 1 = the device image uses the packed layout */
-    int32_t pad;
+    int32_t aligned;         /* 1 = the device image is relocated with two-word structures at even words */
     uint64_t canonical_words;   /* paper-layout buffer size in words */
     uint64_t device_bytes;      /* device image size */
     uint64_t occupied_voxels;
@@ -376,7 +388,9 @@ int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_h
  * exits; the call itself never calls cudaMalloc or cudaFree.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current: make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the process; it
+ *     stays valid until the device's primary context is destroyed
+ *     (cudaDeviceReset), after which this entry point must not be called.
  *   - All calls share the array; each zeroes the counter on its stream before
  *     its launch, so calls whose kernels overlap on the GPU race: issue them
  *     one after another (e.g. on one stream).

@@ -61,7 +61,7 @@ class _TraceOpts(ctypes.Structure):
 
 class _Stats(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_uint32), ("n_node_levels", ctypes.c_uint32), ("log2_dim", ctypes.c_uint32 * 3),
-                ("specialized", ctypes.c_int32), ("packed", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("specialized", ctypes.c_int32), ("packed", ctypes.c_int32), ("aligned", ctypes.c_int32),
                 ("canonical_words", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("occupied_voxels", ctypes.c_uint64),
                 ("level_words", ctypes.c_uint64 * MAX_LEVELS), ("level_nodes", ctypes.c_uint64 * MAX_LEVELS),
@@ -329,7 +329,8 @@ class Volume:
         n = s.n_levels
         return {
             "n_levels": n, "n_node_levels": s.n_node_levels, "log2_dim": tuple(s.log2_dim),
-            "specialized": bool(s.specialized), "packed": bool(s.packed), "canonical_words": s.canonical_words,
+            "specialized": bool(s.specialized), "packed": bool(s.packed), "aligned": bool(s.aligned),
+            "canonical_words": s.canonical_words,
             "canonical_bytes": 4 * s.canonical_words, "device_bytes": s.device_bytes,
             "occupied_voxels": s.occupied_voxels, "level_words": list(s.level_words)[:n],
             "level_nodes": list(s.level_nodes)[:n], "build_ms": s.build_ms, "upload_ms": s.upload_ms,

@@ -162,20 +162,23 @@ int upload(Volume& V, const vx_build_opts& o, bool allow_packed) {
     DeviceScope ds(dev);
     if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
     V.device = dev;
-    const uint64_t bytes = V.built.words.size() * sizeof(uint32_t);
-    std::vector<uint32_t> packed;
-    const bool use_packed = allow_packed && pack_device_image(V.spec, V.built.words, packed);
-    V.packed = use_packed ? 1 : 0;
-    const uint32_t* src_words = use_packed ? packed.data() : V.built.words.data();
+    std::vector<uint32_t> image;
+    bool packed = false;
+    const bool relocated = allow_packed && make_device_image(V.spec, V.built.words, image, &packed);
+    V.packed = relocated && packed ? 1 : 0;
+    V.aligned = relocated ? 1 : 0;
+    const std::vector<uint32_t>& src = relocated ? image : V.built.words;
+    const uint64_t bytes = src.size() * sizeof(uint32_t);
     cudaError_t e = cudaMalloc((void**)&V.d_pool, bytes);
     if (e) return cuda_fail(e, "cudaMalloc (device image)");
-    e = cudaMemcpy(V.d_pool, src_words, bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(V.d_pool, src.data(), bytes, cudaMemcpyHostToDevice);
     if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMemcpy (device image)"); }
-    V.pool_words = V.built.words.size();
-    e = cudaMalloc((void**)&V.d_queue, kQueueRing * sizeof(unsigned long long));
+    V.pool_words = src.size();
+    e = cudaMalloc((void**)&V.d_queue, (kQueueRing + kQueueCaptured) * sizeof(unsigned long long));
     if (e) { cudaFree(V.d_pool); V.d_pool = nullptr; return cuda_fail(e, "cudaMalloc (queue counters)"); }
     V.stats.device_bytes = bytes;
     V.stats.packed = V.packed;
+    V.stats.aligned = V.aligned;
     return VX_OK;
 }
 }  // namespace
@@ -481,9 +484,19 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
             consider(c);
         }
     }
+    // sort granularities; the key keeps at most 5 bits per axis, so at large
+    // grids several g give the same key cells (tried once)
     const int maxg = std::min(V.spec.ldim[0], std::min(V.spec.ldim[1], V.spec.ldim[2]));
+    int last_shift = -1;
     for (int g : {2, 3, 4, 5, 6, 7}) {
         if (g > maxg) break;
+        int shift = 0;
+        for (int i = 0; i < 3; i++) {
+            const int b = std::min(std::max(V.spec.ldim[i] - g, 0), 5);
+            shift = shift * 16 + (V.spec.ldim[i] - b);
+        }
+        if (shift == last_shift) continue;
+        last_shift = shift;
         vx_trace_opts c = cur; c.sort_cell_log2 = g; consider(c);
     }
     // two rounds of coordinate descent over the persistent-kernel knobs (a

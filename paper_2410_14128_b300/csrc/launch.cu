@@ -34,6 +34,8 @@ CamDev to_dev(const CameraParams& c) {
     return d;
 }
 
+Img img_of(const Volume& v) { return Img{v.d_pool, v.packed, (uint32_t)v.pool_words, v.aligned}; }
+
 int pick_block(const vx_trace_opts* o) {
     int b = (o && o->block > 0) ? o->block : 256;
     return b;
@@ -98,6 +100,40 @@ __global__ void __launch_bounds__(256) k_ao_rays(const float4* __restrict__ rays
 }  // namespace
 
 void register_kernel_set(const KernelSet* ks) { registry().push_back(ks); }
+
+unsigned long long* Volume::queue_counter(void* stream) const {
+    if (!d_queue) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) return nullptr;
+    if (cs == cudaStreamCaptureStatusActive) {
+        const uint32_t k = captured_slot.fetch_add(1, std::memory_order_relaxed);
+        if (k >= (uint32_t)kQueueCaptured) return nullptr;
+        return d_queue + kQueueRing + k;
+    }
+    return d_queue + (queue_slot.fetch_add(1, std::memory_order_relaxed) % kQueueRing);
+}
+
+void prefer_carveout(const void* kernel, size_t smem_per_block, int block) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void*, int>, int>> done;  // ((kernel, device), percent) set
+    int dev = 0;
+    if (cudaGetDevice(&dev)) return;
+    const int blocks = block > 0 ? (1024 + block - 1) / block : 1;
+    const size_t need = (size_t)blocks * (smem_per_block + 1024);  // 1 KiB per block is reserved
+    const size_t max_smem = 228u * 1024u;
+    int pct = (int)((need * 100 + max_smem - 1) / max_smem);
+    if (pct > 100) pct = 100;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first.first == kernel && d.first.second == dev) {
+            if (d.second == pct) return;
+            d.second = pct;
+            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            return;
+        }
+    done.emplace_back(std::make_pair(kernel, dev), pct);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
 
 int launch_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, int spp, float eps, float tmax,
               vx_ray* out, void* stream) {
@@ -167,19 +203,20 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     }
     int e;
     if (mode == VX_MODE_PERSISTENT) {
-        unsigned long long* next = v.queue_counter();
+        unsigned long long* next = v.queue_counter(st);
         if (!next) {
             if (scratch) cudaFreeAsync(scratch, st);
-            return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+            return fail(VX_EUNSUPPORTED, "no queue counter for the persistent kernel (at most %d captured "
+                        "persistent launches per volume)", kQueueCaptured);
         }
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
         const int smem_top = o ? o->smem_top : 0;
-        e = v.kernels->trace_persistent(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), order, n, hits,
+        e = v.kernels->trace_persistent(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits,
                                         layout, block, bps, refill, burst, restart, smem_top, st, next);
     } else {
-        e = v.kernels->trace(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), order, n, hits, layout,
+        e = v.kernels->trace(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits, layout,
                              block, restart, st);
     }
     if (scratch) cudaFreeAsync(scratch, st);
@@ -191,7 +228,7 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
                        const vx_trace_opts* o, void* stream, unsigned long long* counters, uint32_t* sectors) {
     const int block = pick_block(o);
     const int restart = o ? o->restart : 0;
-    int e = v.kernels->trace_count(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, reinterpret_cast<const float4*>(rays), n, hits, layout,
+    int e = v.kernels->trace_count(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), n, hits, layout,
                                    block, restart, (cudaStream_t)stream, counters, sectors);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
     return VX_OK;
@@ -205,14 +242,16 @@ int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t
     const int block = (o && o->block > 0) ? o->block : (mode == VX_MODE_PERSISTENT ? pick_block(o) : 128);
     int e;
     if (mode == VX_MODE_PERSISTENT) {
-        unsigned long long* next = v.queue_counter();
-        if (!next) return fail(VX_ECUDA, "no queue counter for the persistent kernel");
+        unsigned long long* next = v.queue_counter(stream);
+        if (!next)
+            return fail(VX_EUNSUPPORTED, "no queue counter for the persistent kernel (at most %d captured "
+                        "persistent launches per volume)", kQueueCaptured);
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
-        e = v.kernels->render_persistent(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, to_dev(cp), i0, n, hits, layout, block,
+        e = v.kernels->render_persistent(v.spec.fmt, img_of(v), to_dev(cp), i0, n, hits, layout, block,
                                          refill, burst, (cudaStream_t)stream, next);
     } else {
-        e = v.kernels->render(v.spec.fmt, Img{v.d_pool, v.packed, (uint32_t)v.pool_words}, to_dev(cp), i0, n, hits, layout, block,
+        e = v.kernels->render(v.spec.fmt, img_of(v), to_dev(cp), i0, n, hits, layout, block,
                               (cudaStream_t)stream);
     }
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -258,7 +297,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         Sub* g = nullptr;
         for (Sub& s2 : subs)
             if (s2.ks == it.v->kernels && same_params(s2.v0->spec.fmt, it.v->spec.fmt) &&
-                s2.d.packed == it.v->packed && s2.d.count < kBatchMax) {
+                s2.d.packed == it.v->packed && s2.d.aligned == it.v->aligned && s2.d.count < kBatchMax) {
                 g = &s2;
                 break;
             }
@@ -267,6 +306,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
             g = &subs.back();
             g->d.count = 0;
             g->d.packed = it.v->packed;
+            g->d.aligned = it.v->aligned;
             g->d.start[0] = 0;
         }
         const uint32_t k = g->d.count++;
@@ -310,8 +350,13 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
     // and the next one's blocks start as the previous one's retire (separate
     // streams), so no SM waits for a slower group.
     std::vector<int> grids(nsub);
+    std::vector<unsigned long long*> nexts(nsub);
     for (int i = 0; i < nsub; i++) {
         const Sub& g = subs[i];
+        nexts[i] = g.v0->queue_counter(st);  // the fork streams inherit the caller's capture state
+        if (!nexts[i])
+            return fail(VX_EUNSUPPORTED, "no queue counter for the batched kernel (at most %d captured "
+                        "persistent launches per volume)", kQueueCaptured);
         int per_sm = 1;
         int rc = g.ks->resident_blocks(g.v0->spec.fmt, layout, block, &per_sm);
         if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
@@ -334,17 +379,18 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         Sub& g = subs[i];
         cudaStream_t fs = F.s[i % kForkStreams];
         const bool timed = events && (uint32_t)(2 * i + 1) < n_events;
-        if (timed && (e = cudaEventRecord((cudaEvent_t)events[2 * i], fs))) {
+        // cudaEventRecordExternal: inside a stream capture the record becomes
+        // an event node of the graph (a plain record there is only an edge)
+        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i], fs, cudaEventRecordExternal))) {
             rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
             break;
         }
-        unsigned long long* next = g.v0->queue_counter();
-        int lr = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, grids[i], refill, burst, fs, next);
+        int lr = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, grids[i], refill, burst, fs, nexts[i]);
         if (lr) {
             rc = fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)lr));
             break;
         }
-        if (timed && (e = cudaEventRecord((cudaEvent_t)events[2 * i + 1], fs))) {
+        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i + 1], fs, cudaEventRecordExternal))) {
             rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
             break;
         }

@@ -135,10 +135,10 @@ int trace_noalloc(const Volume& V, const vx_ray* rays, uint64_t n, void* hits, i
     DynF f;
     f.p = V.spec.fmt;
     if (layout == VX_HIT_FULL)
-        k_trace_noalloc<0><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<0><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words, V.aligned}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     else
-        k_trace_noalloc<1><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words}, reinterpret_cast<const float4*>(rays),
+        k_trace_noalloc<1><<<(unsigned)grid, block, sm, st>>>(f, Img{V.d_pool, V.packed, (uint32_t)V.pool_words, V.aligned}, reinterpret_cast<const float4*>(rays),
                                                               (uint32_t)n, hits, next, kDefaultRefill, kDefaultBurst);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "vx_trace_noalloc launch: %s", cudaGetErrorString(e));

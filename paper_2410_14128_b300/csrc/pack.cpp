@@ -1,20 +1,23 @@
 // pack.cpp -- the device image of a volume.
 //
-// The canonical buffer follows the paper's layout (Sec. 3.3), where reaching
-// an SVDAG child costs two dependent reads: the child pointer in the parent,
-// then the child's masks word (and, at the last octree level, a third read:
-// the leaf's terminating integer).  The packed device image keeps every
-// offset of the canonical buffer and rewrites three kinds of words in place:
-//   - a pointer to an SVDAG node p becomes (valid mask of p) << 24 | p;
-//   - an SVDAG node's slot for a leaf child holds the leaf's terminating
-//     integer itself instead of a pointer to it;
-//   - word 0 (root pointer) and Raw / DF cells / SVO leaf words that point
-//     at an SVDAG root follow the first rule.
-// It needs every offset below 2^24 words (64 MiB); larger volumes keep the
-// canonical words on the device (the kernels are told which layout they
-// read).
+// The canonical buffer follows the paper's layout (Sec. 3.3).  The device
+// image holds the same structures -- Raw and DF cell arrays, SVO root entries
+// and child lists, SVDAG nodes -- in the same (canonical) order, relocated
+// with every pointer rewritten to the new offsets, and changed in two ways:
+//   - aligned: every DF cell array, SVO root entry and SVO child list starts
+//     at an even word, so that a DF cell {terminating integer, distance} and
+//     an SVO node entry {pointer, masks} are each read with one 8-byte load
+//     (one zero word of padding where needed);
+//   - packed (a format with an SVDAG level whose image stays below 2^24
+//     words): a pointer to an SVDAG node carries the node's valid mask in
+//     bits 24..31, which saves the dependent read of the node's masks word on
+//     every descent, and an SVDAG slot of a leaf child holds the leaf's
+//     terminating integer itself, so the leaf words are not stored at all.
+// vx_canonical keeps returning the paper's layout; canonical_device uploads
+// it unchanged (then the kernels read it with 4-byte loads).
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "vx_internal.hpp"
@@ -22,118 +25,218 @@
 namespace vx {
 namespace {
 
-class Packer {
+enum : uint8_t { I_CELLS, I_DF, I_SVO_ROOT, I_SVO_LIST, I_DAG, I_DAG_LEAF };
+
+struct Item {
+    uint32_t old;  // canonical offset of the structure's first word
+    uint32_t len;  // words
+    uint8_t kind, level, depth, align;  // depth: SVO list entries' / SVDAG node's octree depth
+};
+
+class Relocator {
   public:
-    Packer(const Spec& sp, const std::vector<uint32_t>& in, std::vector<uint32_t>& out)
-        : sp_(sp), in_(in), out_(out), seen_(in.size(), 0) {
+    Relocator(const Spec& sp, const std::vector<uint32_t>& in) : sp_(sp), in_(in), seen_(in.size(), 0) {
         nlev_ = (int)sp.lv.size();
     }
 
-    bool run() {
-        out_ = in_;
-        if (in_[0] == 0) return true;
-        out_[0] = ptr_for(0, in_[0]);
+    // Builds the image; false if the buffer is not a well-formed volume of
+    // the spec or an offset would not fit 32 bits (the caller then uploads
+    // the canonical words).
+    bool run(std::vector<uint32_t>& out, bool& packed) {
+        packed = false;
+        if (in_.empty()) return false;
+        if (in_[0] == 0) {
+            out.assign(1, 0u);
+            return true;
+        }
         level(0, in_[0]);
+        if (!ok_) return false;
+        std::sort(items_.begin(), items_.end(), [](const Item& a, const Item& b) { return a.old < b.old; });
+        bool any_dag = false;
+        for (const Level& L : sp_.lv) any_dag |= L.kind == K_DAG;
+        uint64_t size = assign(any_dag);
+        packed = any_dag && size < (1ull << 24);
+        if (any_dag && !packed) size = assign(false);
+        if (size > 0xFFFFFFFFull) return false;
+        out.assign((size_t)size, 0u);
+        out[0] = ptr_to(0, in_[0], packed);
+        for (const Item& it : items_) write(it, out, packed);
         return ok_;
     }
 
   private:
-    // The word a parent stores for the root of level k's sub-volume at p.
-    uint32_t ptr_for(int k, uint32_t p) const {
-        if (sp_.lv[k].kind == K_DAG) return ((in_[p] & 0xFFu) << 24) | p;
-        return p;
-    }
     bool check(uint64_t p, uint64_t n) {
         if (p == 0 || p + n > in_.size()) ok_ = false;
         return ok_;
     }
-    void level(int k, uint32_t p) {
-        if (!ok_ || seen_[p]) return;
+    bool first_visit(uint32_t p) {
+        if (seen_[p]) return false;
         seen_[p] = 1;
+        return true;
+    }
+    void add(uint32_t p, uint64_t n, uint8_t kind, int k, int depth, int align) {
+        items_.push_back(Item{p, (uint32_t)n, kind, (uint8_t)k, (uint8_t)depth, (uint8_t)align});
+    }
+
+    // ---- pass 1: every structure reachable from the root, once ----
+    void level(int k, uint32_t p) {
+        if (!ok_ || !check(p, 1) || !first_visit(p)) return;
         const Level& L = sp_.lv[k];
         const bool last = k == nlev_ - 1;
         if (L.kind == K_RAW || L.kind == K_DF) {
             const uint64_t cells = 1ull << (L.e[0] + L.e[1] + L.e[2]);
             const uint64_t wpc = L.kind == K_DF ? 2 : 1;  // DF: {terminating integer, distance}
-            if (!check(p, wpc * cells) || last) return;
-            for (uint64_t i = 0; i < cells; i++) {
+            if (!check(p, wpc * cells)) return;
+            add(p, wpc * cells, L.kind == K_DF ? I_DF : I_CELLS, k, 0, L.kind == K_DF ? 2 : 1);
+            if (last) return;
+            for (uint64_t i = 0; i < cells && ok_; i++) {
                 const uint32_t w = in_[p + wpc * i];
-                if (!w) continue;
-                level(k + 1, w);
-                out_[p + wpc * i] = ptr_for(k + 1, w);
+                if (w) level(k + 1, w);
             }
         } else if (L.kind == K_SVO) {
-            svo(k, p, 0);
+            if (!check(p, 2)) return;
+            add(p, 2, I_SVO_ROOT, k, 0, 2);
+            svo_list(k, in_[p], in_[p + 1] & 0xFFu, 1);
         } else {
             dag(k, p, 0);
         }
     }
-    void svo(int k, uint32_t p, int depth) {
-        if (!check(p, 2)) return;
+    // child list at `first` of a node with valid mask `valid`: its entries sit
+    // at octree depth dd (leaves when dd == L)
+    void svo_list(int k, uint32_t first, uint32_t valid, int dd) {
+        const uint32_t cnt = (uint32_t)__builtin_popcount(valid);
+        if (!ok_ || cnt == 0 || !check(first, 2ull * cnt) || !first_visit(first)) return;
         const int L = sp_.lv[k].e[0];
         const bool last = k == nlev_ - 1;
-        const uint32_t first = in_[p], valid = in_[p + 1] & 0xFFu;
-        const uint32_t cnt = __builtin_popcount(valid);
-        if (!check(first, 2ull * cnt)) return;
-        for (uint32_t r = 0; r < cnt; r++) {
+        add(first, 2ull * cnt, I_SVO_LIST, k, dd, 2);
+        for (uint32_t r = 0; r < cnt && ok_; r++) {
             const uint32_t c = first + 2 * r;
-            if (depth + 1 == L) {
-                if (last) continue;
-                const uint32_t term = in_[c];
-                level(k + 1, term);
-                out_[c] = ptr_for(k + 1, term);
+            if (dd == L) {
+                if (!last) level(k + 1, in_[c]);
             } else {
-                svo(k, c, depth + 1);
+                svo_list(k, in_[c], in_[c + 1] & 0xFFu, dd + 1);
             }
         }
     }
-    void dag(int k, uint32_t p, int depth) {
-        if (!check(p, 1)) return;
-        if (depth > 0) {  // roots are marked by level()
-            if (seen_[p]) return;
-            seen_[p] = 1;
-        }
+    void dag(int k, uint32_t p, int d) {
+        if (!ok_ || !check(p, 1)) return;
+        if (d > 0 && !first_visit(p)) return;  // roots were marked by level()
         const int L = sp_.lv[k].e[0];
         const bool last = k == nlev_ - 1;
-        const uint32_t valid = in_[p] & 0xFFu;
-        const uint32_t cnt = __builtin_popcount(valid);
+        const uint32_t cnt = (uint32_t)__builtin_popcount(in_[p] & 0xFFu);
         if (!check(p, 1ull + cnt)) return;
-        for (uint32_t r = 0; r < cnt; r++) {
-            const uint32_t slot = p + 1 + r;
-            const uint32_t c = in_[slot];
+        add(p, 1ull + cnt, I_DAG, k, d, 1);
+        for (uint32_t r = 0; r < cnt && ok_; r++) {
+            const uint32_t c = in_[p + 1 + r];
             if (!check(c, 1)) return;
-            if (depth + 1 == L) {
-                const uint32_t term = in_[c];
-                if (last) {
-                    out_[slot] = term;
-                } else {
-                    level(k + 1, term);
-                    out_[slot] = ptr_for(k + 1, term);
-                }
+            if (d + 1 == L) {
+                if (!first_visit(c)) continue;
+                add(c, 1, I_DAG_LEAF, k, L, 1);
+                if (!last) level(k + 1, in_[c]);
             } else {
-                dag(k, c, depth + 1);
-                out_[slot] = ((in_[c] & 0xFFu) << 24) | c;
+                dag(k, c, d + 1);
             }
+        }
+    }
+
+    // ---- new offsets, in canonical order; returns the image size ----
+    uint64_t assign(bool packed) {
+        newoff_.assign(items_.size(), 0u);
+        uint64_t cur = 1;  // word 0: root pointer
+        for (size_t i = 0; i < items_.size(); i++) {
+            const Item& it = items_[i];
+            if (packed && it.kind == I_DAG_LEAF) continue;  // inlined into the slots
+            if (it.align == 2 && (cur & 1)) cur++;
+            newoff_[i] = (uint32_t)std::min<uint64_t>(cur, 0xFFFFFFFFull);
+            cur += it.len;
+        }
+        return cur;
+    }
+    uint32_t where(uint32_t old) {
+        auto pos = std::lower_bound(items_.begin(), items_.end(), old,
+                                    [](const Item& a, uint32_t v) { return a.old < v; });
+        if (pos == items_.end() || pos->old != old) {
+            ok_ = false;
+            return 0;
+        }
+        return newoff_[pos - items_.begin()];
+    }
+    // the word a parent stores for the root of level k's sub-volume at canonical p
+    uint32_t ptr_to(int k, uint32_t p, bool packed) {
+        const uint32_t n = where(p);
+        if (packed && sp_.lv[k].kind == K_DAG) return ((in_[p] & 0xFFu) << 24) | n;
+        return n;
+    }
+
+    // ---- pass 2: copy each structure, pointers rewritten ----
+    void write(const Item& it, std::vector<uint32_t>& out, bool packed) {
+        if (packed && it.kind == I_DAG_LEAF) return;
+        const uint32_t* src = in_.data() + it.old;
+        uint32_t* dst = out.data() + where(it.old);
+        const int k = it.level;
+        const bool last = k == nlev_ - 1;
+        const int L = sp_.lv[k].e[0];
+        switch (it.kind) {
+            case I_CELLS:
+                for (uint32_t i = 0; i < it.len; i++) dst[i] = (last || !src[i]) ? src[i] : ptr_to(k + 1, src[i], packed);
+                break;
+            case I_DF:
+                for (uint32_t i = 0; i < it.len; i += 2) {
+                    dst[i] = (last || !src[i]) ? src[i] : ptr_to(k + 1, src[i], packed);
+                    dst[i + 1] = src[i + 1];
+                }
+                break;
+            case I_SVO_ROOT:
+                dst[0] = where(src[0]);
+                dst[1] = src[1];
+                break;
+            case I_SVO_LIST:
+                for (uint32_t i = 0; i < it.len; i += 2) {
+                    if (it.depth == L) dst[i] = last ? src[i] : ptr_to(k + 1, src[i], packed);
+                    else dst[i] = where(src[i]);
+                    dst[i + 1] = src[i + 1];
+                }
+                break;
+            case I_DAG:
+                dst[0] = src[0];
+                for (uint32_t r = 1; r < it.len; r++) {
+                    const uint32_t c = src[r];
+                    if (it.depth + 1 == L) {
+                        if (packed) dst[r] = last ? in_[c] : ptr_to(k + 1, in_[c], true);
+                        else dst[r] = where(c);
+                    } else {
+                        const uint32_t n = where(c);
+                        dst[r] = packed ? (((in_[c] & 0xFFu) << 24) | n) : n;
+                    }
+                }
+                break;
+            case I_DAG_LEAF:
+                dst[0] = last ? src[0] : ptr_to(k + 1, src[0], false);
+                break;
         }
     }
 
     const Spec& sp_;
     const std::vector<uint32_t>& in_;
-    std::vector<uint32_t>& out_;
     std::vector<uint8_t> seen_;
+    std::vector<Item> items_;
+    std::vector<uint32_t> newoff_;
     int nlev_;
     bool ok_ = true;
 };
 
 }  // namespace
 
-bool pack_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out) {
-    if (canonical.size() >= (1u << 24)) return false;
-    bool any_dag = false;
-    for (const Level& L : spec.lv) any_dag |= L.kind == K_DAG;
-    if (!any_dag) return false;  // nothing to rewrite
-    Packer p(spec, canonical, out);
-    return p.run();
+bool make_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out,
+                       bool* packed) {
+    bool pk = false;
+    Relocator r(spec, canonical);
+    if (!r.run(out, pk)) {
+        out.clear();
+        return false;
+    }
+    *packed = pk;
+    return true;
 }
 
 }  // namespace vx

@@ -2,7 +2,9 @@
 //
 // Key of a ray = direction octant (3 bits) above the Morton code (x lowest,
 // Fig. 5 order) of its origin's cell of side 2^g voxels, the origin clamped
-// into the grid.  Rays with equal keys start close together and head the
+// into the grid.  The code keeps at most 5 bits per axis (2^18 bins in all):
+// when an axis has more than 5 bits of cells, the key takes its 5 coarsest
+// ones, i.e. cells of side 2^(log2 dim - 5) on that axis.  Rays with equal keys start close together and head the
 // same way, so a warp that traces consecutive sorted rays reads the same
 // nodes and takes similar paths.  A counting sort by key (histogram,
 // exclusive scan, scatter) yields `order`, the ray indices in key order; the
@@ -19,7 +21,8 @@ namespace {
 struct KeyParams {
     int ld[3];
     int g;      // cell side 2^g
-    int kb[3];  // Morton bits per axis
+    int kb[3];  // Morton bits per axis: min(max(ld - g, 0), 5)
+    int sh[3];  // shift of a voxel coordinate to its key cell: ld - kb (= g unless capped)
     int mbits;  // kb[0] + kb[1] + kb[2]
 };
 
@@ -32,7 +35,7 @@ __device__ __forceinline__ uint32_t ray_key(const float4 a, const float4 b, cons
         const float n = (float)(1 << k.ld[i]);
         float v = fminf(fmaxf(o[i], 0.0f), n - 1.0f);  // NaN -> 0
         if (!(v == v)) v = 0.0f;
-        cell[i] = ((uint32_t)v) >> k.g;
+        cell[i] = ((uint32_t)v) >> k.sh[i];
     }
     uint32_t m = 0;
     int bit = 0;
@@ -163,6 +166,7 @@ int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* sc
         if (b < 0) b = 0;
         if (b > 5) b = 5;
         kp.kb[i] = b;
+        kp.sh[i] = ldim[i] - b;
         kp.mbits += b;
     }
     const uint32_t nbins = 8u << kp.mbits;

@@ -259,13 +259,17 @@ __device__ __forceinline__ bool near32(float x, float y) {
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t* __restrict__ pool, uint32_t i) { return __ldg(pool + i); }
 
-// A volume's device image: its words, and whether they are in the packed
-// layout (pack.cpp: pointers to SVDAG nodes carry the node's valid mask in
-// bits 24..31; SVDAG slots of leaf children hold the terminating integer).
+// A volume's device image: its words, whether they are in the packed layout
+// (pack.cpp: pointers to SVDAG nodes carry the node's valid mask in bits
+// 24..31; SVDAG slots of leaf children hold the terminating integer), and
+// whether two-word structures start at even words (then {pointer, masks} of
+// an SVO node and {terminating integer, distance} of a DF cell are one
+// 8-byte load).
 struct Img {
     const uint32_t* w;
     int packed;
-    uint32_t n;  // words in the image (the instrumented kernels check every read against it)
+    uint32_t n;   // words in the image (the instrumented kernels check every read against it)
+    int aligned;  // DF cell arrays, SVO root entries and SVO child lists start at even words
 };
 constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 
@@ -298,18 +302,27 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // look-ups read them there.
 //
 // Dynamic shared memory of every walker kernel: first the node stacks of the
-// block's threads, entry e of thread t at vx_dyn_smem[e * blockDim.x + t]
-// (stack_entries(J) entries of 8 bytes per thread), then, in a persistent
-// kernel that stages the top level, its words.  Lanes of a warp touch
-// consecutive 8-byte entries whatever entry each reads, so the accesses are
-// free of bank conflicts, and the stack takes no L1 lines from node reads.
+// block's threads, entry e of thread t at vx_dyn_smem[t * stack_stride(J) +
+// e] (8-byte entries), then, in a persistent kernel that stages the top
+// level, its words.  The stride is odd, so the 16 lanes of a half-warp that
+// read the same entry touch 16 distinct 8-byte bank pairs (no bank
+// conflicts), and a thread reaches any entry from one base register plus a
+// constant; the stack takes no L1 lines from node reads.
 extern __shared__ __align__(16) uint2 vx_dyn_smem[];
 constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB: R(4,4,4) or D(4,4,4,M)
 
+// Shared-memory carveout preference of a walker kernel, in percent of the
+// SM's maximum (228 KiB): what its resident blocks need (the kernels are
+// compiled for 1024 resident threads per SM), so that the rest of the SM's
+// on-chip memory stays L1 for node reads.  Set once per kernel and value
+// (launch.cu).
+void prefer_carveout(const void* kernel, size_t smem_per_block, int block);
+
 // Entries per thread: one {pointer, valid mask} per node level, then two
-// holding the ray's start voxel.
+// holding the ray's start voxel; the stride rounds that up to an odd count.
 __host__ __device__ constexpr uint32_t stack_entries(uint32_t J) { return J + 2u; }
-inline size_t stack_bytes(uint32_t J, int block) { return (size_t)stack_entries(J) * (size_t)block * sizeof(uint2); }
+__host__ __device__ constexpr uint32_t stack_stride(uint32_t J) { return stack_entries(J) | 1u; }
+inline size_t stack_bytes(uint32_t J, int block) { return (size_t)stack_stride(J) * (size_t)block * sizeof(uint2); }
 
 template <bool COUNT, class F, bool RESTART = false, bool TOPS = false>
 struct Walker {
@@ -324,6 +337,7 @@ struct Walker {
     int skip;  // DF level: cells the walk may still enter without a look-up
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
+    uint32_t sb;      // shared-window byte address of this thread's stack entry 0
     uint32_t lim;     // words in the image (checked by the instrumented walker)
     uint32_t* sect;   // instrumented walker: one bit per 32-byte sector of the image it read, or null
     Cnt cnt;
@@ -343,23 +357,43 @@ struct Walker {
         return ldw(pool, i);
     }
 
+    // Words i and i + 1 of the image (an SVO node entry, a DF cell): one
+    // 8-byte load when the image is aligned (i is then even), else two.
+    __device__ __forceinline__ uint2 rd2(const Img& im, uint32_t i) {
+        if (COUNT) {
+            if (i + 1u >= lim || i + 1u < i || (im.aligned && (i & 1u))) {
+                cnt.refused++;
+                return make_uint2(0u, 0u);
+            }
+            if (sect) atomicOr(sect + (i >> 8), 1u << ((i >> 3) & 31u));
+        }
+        if (im.aligned) return __ldg(reinterpret_cast<const uint2*>(im.w + i));
+        return make_uint2(ldw(im.w, i), ldw(im.w, i + 1u));
+    }
+
 
     // Node-stack entry e of this thread (0 <= e < stack_entries(J); entries
     // J and J + 1 hold the start voxel).  Every index the walk forms lies in
     // that range by construction (j only grows by descents below J - 1 and
     // pops to jpop(h) <= j); the instrumented walker also checks it and
     // refuses an access outside it (counted like a refused read).
-    __device__ __forceinline__ int sidx(const F& f, int e) {
+    __device__ __forceinline__ uint32_t saddr(const F& f, int e) {
         if (COUNT && (unsigned)e >= stack_entries((uint32_t)f.J())) {
             cnt.refused++;
             e = 0;
         }
-        return e * (int)blockDim.x + (int)threadIdx.x;
+        return sb + 8u * (uint32_t)e;
     }
-    __device__ __forceinline__ uint2 sget(const F& f, int e) { return vx_dyn_smem[sidx(f, e)]; }
-    __device__ __forceinline__ void sput(const F& f, int e, uint2 v) { vx_dyn_smem[sidx(f, e)] = v; }
+    __device__ __forceinline__ uint2 sget(const F& f, int e) {
+        uint2 v;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr(f, e)));
+        return v;
+    }
+    __device__ __forceinline__ void sput(const F& f, int e, uint2 v) {
+        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(saddr(f, e)), "r"(v.x), "r"(v.y) : "memory");
+    }
     __device__ __forceinline__ const uint32_t* top_words_smem(const F& f) const {
-        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_entries((uint32_t)f.J()) * blockDim.x);
+        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J()) * blockDim.x);
     }
 
     // Node level j: kind, children side (log2 voxels), fanout per axis, and
@@ -393,9 +427,9 @@ struct Walker {
                                  (((uint32_t)(c[2] >> sh) & 1u) << 2);
             const uint32_t rank = __popc(m & ((1u << idx) - 1u));
             if (svo) {
-                const uint32_t a = p + 2u * rank;
-                p = rd(pool, a);
-                m = rd(pool, a + 1) & 0xFFu;
+                const uint2 e2 = rd2(im, p + 2u * rank);
+                p = e2.x;
+                m = e2.y & 0xFFu;
                 VX_CNT(bytes, 8);
             } else {
                 const uint32_t cp = rd(pool, p + 1u + rank);
@@ -413,6 +447,7 @@ struct Walker {
     __device__ __forceinline__ bool start(const F& f, const Img im, const RayIn& ray, HitRec& out) {
         const uint32_t* __restrict__ pool = im.w;
         lim = im.n;
+        sb = (uint32_t)__cvta_generic_to_shared(vx_dyn_smem) + 8u * stack_stride((uint32_t)f.J()) * threadIdx.x;
         r = ray;
         // Invalid rays: any NaN, or an infinite tmin.
         if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
@@ -515,7 +550,7 @@ struct Walker {
         {
             const int k0 = f.kind(0);
             if (k0 == K_RAW || k0 == K_DF) { Pc = root; Mc = 0; }
-            else if (k0 == K_SVO) { Pc = rd(pool, root); Mc = rd(pool, root + 1) & 0xFFu; VX_CNT(bytes, 8); }
+            else if (k0 == K_SVO) { const uint2 e2 = rd2(im, root); Pc = e2.x; Mc = e2.y & 0xFFu; VX_CNT(bytes, 8); }
             else if (im.packed) { Pc = root & kPtrMask; Mc = root >> 24; }
             else { Pc = root; Mc = rd(pool, root) & 0xFFu; VX_CNT(bytes, 4); }
         }
@@ -653,8 +688,16 @@ struct Walker {
         const uint32_t as = is_df ? 2u * idx : idx;  // word of the cell in a staged top level
         const bool staged = TOPS && j == 0;
         uint32_t w = 0, dist = 0;
-        if (is_raw || df_read) w = staged ? top_words_smem(f)[as] : rd(pool, a);
-        if (df_read) dist = staged ? top_words_smem(f)[as + 1] : rd(pool, a + 1);  // same sector as the cell word
+        if (staged) {
+            if (is_raw || df_read) w = top_words_smem(f)[as];
+            if (df_read) dist = top_words_smem(f)[as + 1];
+        } else if (df_read) {  // {terminating integer, distance}: one sector
+            const uint2 cell = rd2(im, a);
+            w = cell.x;
+            dist = cell.y;
+        } else if (is_raw) {
+            w = rd(pool, a);
+        }
         VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
         const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;
         if (is_df) skip = df_read ? (occ ? 0 : (int)dist - 1) : skip - 1;
@@ -667,7 +710,7 @@ struct Walker {
                 if (f.has_svo() && kind == K_SVO) {
                     const uint32_t addr = Pc + 2u * rank;
                     if (lbot(f)) { term = rd(pool, addr); VX_CNT(bytes, 4); }
-                    else { Pn = rd(pool, addr); Mn = rd(pool, addr + 1) & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
+                    else { const uint2 e2 = rd2(im, addr); Pn = e2.x; Mn = e2.y & 0xFFu; node_ready = true; VX_CNT(bytes, 8); }
                 } else {
                     const uint32_t cp = rd(pool, Pc + 1u + rank);
                     if (im.packed) {
@@ -692,7 +735,7 @@ struct Walker {
             if (!node_ready) {
                 const int nk = f.kind(j + 1);
                 if (nk == K_RAW || nk == K_DF) { Pn = term; }
-                else if (f.has_svo() && nk == K_SVO) { Pn = rd(pool, term); Mn = rd(pool, term + 1) & 0xFFu; VX_CNT(bytes, 8); }
+                else if (f.has_svo() && nk == K_SVO) { const uint2 e2 = rd2(im, term); Pn = e2.x; Mn = e2.y & 0xFFu; VX_CNT(bytes, 8); }
                 else if (im.packed) { Pn = term & kPtrMask; Mn = term >> 24; }
                 else { Pn = term; Mn = rd(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
@@ -933,7 +976,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (TS) {
-        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_entries((uint32_t)f.J()) * blockDim.x);
+        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J()) * blockDim.x);
         const uint32_t root = ldw(pool.w, 0);
         if (root != 0)
             for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) top[i] = ldw(pool.w, root + i);
@@ -984,7 +1027,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
 constexpr int kBatchMax = 64;
 struct BatchDesc {
     uint32_t count;
-    int packed;  // layout of every volume of the launch
+    int packed;   // layout of every volume of the launch
+    int aligned;
     const uint32_t* pool[kBatchMax];
     const float4* rays[kBatchMax];
     void* hits[kBatchMax];
@@ -1002,7 +1046,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
     int set = 0;
-    Img pool{nullptr, desc.packed};
+    Img pool{nullptr, desc.packed, 0xFFFFFFFFu, desc.aligned};
     void* hits = nullptr;
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
@@ -1107,6 +1151,9 @@ struct Launch {
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
         const size_t sm = stack_bytes(p.J, block);
+        prefer_carveout(layout == 0 ? (restart ? (const void*)k_trace<F, 0, true> : (const void*)k_trace<F, 0, false>)
+                                    : (restart ? (const void*)k_trace<F, 1, true> : (const void*)k_trace<F, 1, false>),
+                        sm, block);
         if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
         else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
         else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
@@ -1155,6 +1202,9 @@ struct Launch {
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e) return (int)e;
         }
+        prefer_carveout(layout == 0 ? (const void*)k_trace_persistent<F, 0, RS, TS>
+                                    : (const void*)k_trace_persistent<F, 1, RS, TS>,
+                        smem, block);
         int per_sm = per_sm_req;
         if (per_sm <= 0) {
             e = layout == 0
@@ -1194,6 +1244,7 @@ struct Launch {
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
         const size_t sm = stack_bytes(p.J, block);
+        prefer_carveout(layout == 0 ? (const void*)k_trace_batch<F, 0> : (const void*)k_trace_batch<F, 1>, sm, block);
         cudaError_t e = layout == 0
                             ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 0>, block, sm)
                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_trace_batch<F, 1>, block, sm);
@@ -1217,6 +1268,8 @@ struct Launch {
         const F f = make(p);
         int dev = 0, sms = 0, per_sm = 1;
         const size_t sm = stack_bytes(p.J, block);
+        prefer_carveout(layout == 0 ? (const void*)k_render_persistent<F, 0> : (const void*)k_render_persistent<F, 1>,
+                        sm, block);
         cudaError_t e = cudaGetDevice(&dev);
         if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e) return (int)e;
@@ -1246,6 +1299,7 @@ struct Launch {
         const uint64_t grid = (threads + (uint64_t)block - 1) / (uint64_t)block;
         if (grid > 0x7FFFFFFFull) return (int)cudaErrorInvalidConfiguration;
         const size_t sm = stack_bytes(p.J, block);
+        prefer_carveout(layout == 0 ? (const void*)k_render<F, 0> : (const void*)k_render<F, 1>, sm, block);
         if (layout == 0)
             k_render<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
         else

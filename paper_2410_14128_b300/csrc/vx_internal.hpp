@@ -86,9 +86,13 @@ void l1_distance(const uint32_t* terms, const int e[3], uint32_t M, std::vector<
 // buffer, masks, DF distances); fills the per-level word and node counts.
 int validate_canonical(const Spec& spec, const uint32_t* words, uint64_t n, BuildResult* stats);
 
-// Device image in the packed layout (same offsets); false when the volume is
-// too large for it or has no SVDAG level (then the canonical words are used).
-bool pack_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out);
+// Device image (pack.cpp): the canonical structures relocated so that
+// two-word structures start at even words, pointers rewritten; *packed is
+// set when SVDAG pointers also carry masks (images below 2^24 words with an
+// SVDAG level).  False when the buffer is not a well-formed volume of the
+// spec (then the canonical words are uploaded as they are).
+bool make_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out,
+                       bool* packed);
 
 // Decodes the cube (side 2^log2s at x0,y0,z0) from a canonical buffer.
 int decode_cube(const Spec& spec, const uint32_t* words, uint64_t nwords, int64_t x0, int64_t y0, int64_t z0,
@@ -121,7 +125,8 @@ struct Staging {
 
 constexpr int kDefaultRefill = 8;  // persistent kernel: idle lanes before a warp refills
 constexpr int kDefaultBurst = 4;   // persistent kernel: iterations between refill checks
-constexpr int kQueueRing = 256;    // queue counters per volume
+constexpr int kQueueRing = 256;      // queue counters per volume for launches issued directly
+constexpr int kQueueCaptured = 3840;  // further counters, each given to one captured launch for good
 
 struct Volume {
     Spec spec;
@@ -130,7 +135,8 @@ struct Volume {
     int device = -1;
     uint32_t* d_pool = nullptr;
     uint64_t pool_words = 0;
-    int packed = 0;  // device image in the packed layout (pack.cpp)
+    int packed = 0;   // device image in the packed layout (pack.cpp)
+    int aligned = 0;  // device image with two-word structures at even words (pack.cpp)
     bool unvalidated = false;  // loaded without validation: only the checked (counted) trace may read it
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
@@ -138,12 +144,16 @@ struct Volume {
     std::mutex tune_mu;
     bool tuned = false;
     vx_trace_opts tuned_opts{};             // chosen by vx_autotune, used for VX_MODE_AUTO
-    unsigned long long* d_queue = nullptr;  // kQueueRing counters
+    unsigned long long* d_queue = nullptr;  // kQueueRing + kQueueCaptured counters
     mutable std::atomic<uint32_t> queue_slot{0};
-    unsigned long long* queue_counter() const {
-        if (!d_queue) return nullptr;
-        return d_queue + (queue_slot.fetch_add(1, std::memory_order_relaxed) % kQueueRing);
-    }
+    mutable std::atomic<uint32_t> captured_slot{0};
+    // The ray-queue counter of one persistent launch on `stream`.  A launch
+    // issued directly takes the next counter of a ring of kQueueRing, so up
+    // to kQueueRing of them may be in flight at once per volume.  A launch
+    // being captured into a CUDA graph keeps its counter for every replay,
+    // so it gets one of the kQueueCaptured counters that no other launch
+    // ever uses; nullptr once they are used up (or without a device image).
+    unsigned long long* queue_counter(void* stream) const;
 };
 
 const KernelSet* kernels_for(const Spec& sp);

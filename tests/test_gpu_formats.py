@@ -74,10 +74,12 @@ def _trace(vol, rays, **opts):
     return h
 
 
-def _variants(vol, gen):
+def _variants(vol, gen, canon):
     """(label, volume, trace options) for every launch configuration."""
     P, Q = vx.MODE_PLAIN, vx.MODE_PERSISTENT
     return [
+        ("canonical device image, persistent", canon, dict(mode=Q)),
+        ("canonical device image, plain restart", canon, dict(mode=P, restart=True)),
         ("plain", vol, dict(mode=P)),
         ("plain block 64", vol, dict(mode=P, block=64)),
         ("persistent block 128 refill 1 burst 16", vol, dict(mode=Q, block=128, refill=1, burst=16)),
@@ -92,8 +94,8 @@ def _variants(vol, gen):
     ]
 
 
-def _check_configurations(spec, vol, gen, rays, base):
-    for label, v, opts in _variants(vol, gen):
+def _check_configurations(spec, vol, gen, canon, rays, base):
+    for label, v, opts in _variants(vol, gen, canon):
         got = _trace(v, rays, **opts)
         assert torch.equal(got, base), f"{spec}: {label} differs from the persistent trace"
     # the batched kernel (one set) and the instrumented kernel
@@ -146,14 +148,17 @@ def test_format_64(noise64, spec):
     assert vol.stats()["specialized"], spec
     gen = vx.Volume(spec, g, generic_kernel=True)
     assert not gen.stats()["specialized"]
+    canon = vx.Volume(spec, g, canonical_device=True)
+    assert vol.stats()["aligned"] and not canon.stats()["aligned"]
     for name, r in sets.items():
         rd = _dev(r)
         base = _trace(vol, rd, mode=vx.MODE_PERSISTENT)
         _oracle_check(spec, g, None, r, base, None, refs[name])
-        _check_configurations(spec, vol, gen, rd, base)
+        _check_configurations(spec, vol, gen, canon, rd, base)
     _check_render(spec, vol, cam)
     vol.free()
     gen.free()
+    canon.free()
 
 
 # ---------------------------------------------------------------------------
@@ -178,13 +183,16 @@ def test_format_512(terrain512, spec):
     assert vol.stats()["specialized"], spec
     gen = vx.Volume.load(spec, vol.canonical(), generic_kernel=True)
     assert not gen.stats()["specialized"]
+    canon = vx.Volume.load(spec, vol.canonical(), canonical_device=True)
+    assert vol.stats()["aligned"] and not canon.stats()["aligned"]
     for name in sets:
         base = _trace(vol, dev[name], mode=vx.MODE_PERSISTENT)
         _oracle_check(spec, g, None, sets[name], base, samples[name], refs[name])
-        _check_configurations(spec, vol, gen, dev[name], base)
+        _check_configurations(spec, vol, gen, canon, dev[name], base)
     _check_render(spec, vol, cam)
     vol.free()
     gen.free()
+    canon.free()
     torch.cuda.empty_cache()
 
 
@@ -211,23 +219,26 @@ def test_format_2048(scene2048, spec):
     vol = vx.Volume(spec, g8, palette=sc.palette)
     assert vol.stats()["specialized"], spec
     gen = vx.Volume.load(spec, vol.canonical(), generic_kernel=True)
+    canon = vx.Volume.load(spec, vol.canonical(), canonical_device=True)
+    assert vol.stats()["aligned"] and not canon.stats()["aligned"]
     # the full 8-view primary set: sampled rays against the oracle
     base = _trace(vol, prim_d, mode=vx.MODE_PERSISTENT)
     _oracle_check(spec, g8, sc.palette, prim, base, idx, ref)
-    _check_configurations(spec, vol, gen, prim_d, base)
+    _check_configurations(spec, vol, gen, canon, prim_d, base)
     # AO rays from the oracle's primary hits: every one against the oracle
     base_ao = _trace(vol, ao_d, mode=vx.MODE_PERSISTENT)
     _oracle_check(spec, g8, sc.palette, ao, base_ao, None, ao_ref)
-    _check_configurations(spec, vol, gen, ao_d, base_ao)
+    _check_configurations(spec, vol, gen, canon, ao_d, base_ao)
     # the benchmark's own AO workload at full size (GPU-generated from the
     # format's primary hits): every configuration identical
     full = torch.cat([vx.raygen_ao(prim_d[k * W * H:(k + 1) * W * H], base[k * W * H:(k + 1) * W * H],
                                    seed=2048, spp=8) for k in range(len(cams))])
     base_full = _trace(vol, full, mode=vx.MODE_PERSISTENT)
-    for label, v, opts in _variants(vol, gen):
+    for label, v, opts in _variants(vol, gen, canon):
         assert torch.equal(_trace(v, full, **opts), base_full), f"{spec}: {label} differs on the full AO set"
     del full, base_full
     _check_render(spec, vol, cams[0])
     vol.free()
     gen.free()
+    canon.free()
     torch.cuda.empty_cache()
