@@ -243,7 +243,15 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *          its root after leaving one of its nodes (same results, no stack
  *          per octree depth, redundant node reads).  Used by vx_trace and
  *          vx_trace_counted; vx_render, vx_trace_batch and vx_trace_noalloc
- *          always keep the stack.  Any other value: VX_EINVAL.
+ *          always keep the stack.  Any other value: VX_EINVAL;
+ *   short_stack 0 = the full node stack (one entry per node level); D in
+ *          {1, 2, 4, 8} = keep each format level's root node and, for the
+ *          octree levels below it, only a ring of the D most recently entered
+ *          nodes: leaving a node whose ancestor fell out of the ring walks
+ *          that format level again from its root (the restart of Sec. 4.4),
+ *          so results are the same with less per-ray state.  Used by vx_trace
+ *          (plain and persistent; not with smem_top, which it turns off).
+ *          VX_EINVAL for other values or together with restart = 1.
  * Persistent launches (and the kernels of vx_trace_batch) each need a
  * ray-queue counter of the volume.  A launch issued directly takes one from a
  * ring of 256 per volume, so at most 256 of them may be in flight at once per
@@ -261,6 +269,7 @@ typedef struct vx_trace_opts {
     int32_t burst;
     int32_t sort_cell_log2;
     int32_t restart;
+    int32_t short_stack;
 } vx_trace_opts;
 
 /* Size and build statistics of a volume.  Level k counts the words written
@@ -330,9 +339,9 @@ int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, in
  * write them.  The call enqueues work on `stream` and returns; it allocates
  * nothing and does not synchronise, so it can be captured into a CUDA graph
  * (make one uncaptured call per device first: it creates the library's
- * fork streams).  opts: refill/burst/block as for vx_trace (NULL or
- * VX_MODE_AUTO: the first volume's tuned persistent options, else the
- * defaults); sorting is not supported
+ * fork streams).  opts: refill/burst/block as for vx_trace for every group
+ * (NULL or VX_MODE_AUTO: each group's volume's tuned persistent options,
+ * else the defaults); sorting is not supported
  * here (VX_EUNSUPPORTED).  Calls for one device are enqueued one at a time.
  * (Not in the paper: it traces one frame of one format at a time.) */
 typedef struct vx_batch_item {

@@ -56,7 +56,7 @@ class _BuildOpts(ctypes.Structure):
 class _TraceOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("smem_top", ctypes.c_int32), ("refill", ctypes.c_int32), ("burst", ctypes.c_int32),
-                ("sort_cell_log2", ctypes.c_int32), ("restart", ctypes.c_int32)]
+                ("sort_cell_log2", ctypes.c_int32), ("restart", ctypes.c_int32), ("short_stack", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -158,8 +158,10 @@ def compiled_formats() -> list[str]:
     return [arr[i].decode() for i in range(n.value)]
 
 
-def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False, smem_top=False):
+def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, restart=False, smem_top=False,
+          short_stack=0):
     o = _TraceOpts()
+    o.short_stack = short_stack
     o.mode, o.block, o.blocks_per_sm, o.refill, o.burst = mode, block, blocks_per_sm, refill, burst
     o.smem_top = int(smem_top)
     o.sort_cell_log2 = sort
@@ -170,7 +172,7 @@ def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, r
 def _opts_dict(o: _TraceOpts) -> dict:
     return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
             "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
-            "smem_top": bool(o.smem_top)}
+            "smem_top": bool(o.smem_top), "short_stack": o.short_stack}
 
 
 def _camera(cam: dict) -> _Camera:

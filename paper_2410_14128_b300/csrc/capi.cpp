@@ -76,6 +76,10 @@ int check_opts(const vx_trace_opts* o) {
         return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
     if (o->restart != 0 && o->restart != 1) return fail(VX_EINVAL, "restart must be 0 or 1, got %d", o->restart);
     if (o->smem_top != 0 && o->smem_top != 1) return fail(VX_EINVAL, "smem_top must be 0 or 1, got %d", o->smem_top);
+    if (o->short_stack != 0 && o->short_stack != 1 && o->short_stack != 2 && o->short_stack != 4 &&
+        o->short_stack != 8)
+        return fail(VX_EINVAL, "short_stack must be 0, 1, 2, 4 or 8, got %d", o->short_stack);
+    if (o->short_stack && o->restart) return fail(VX_EINVAL, "short_stack and restart exclude each other");
     return VX_OK;
 }
 
@@ -474,11 +478,22 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
     bool deep_octree = false;
     for (const Level& L : V.spec.lv) deep_octree |= (L.kind == K_SVO || L.kind == K_DAG) && L.e[0] >= 2;
     if (deep_octree) { vx_trace_opts c = cur; c.restart = 1; consider(c); }
+    // a short stack between the two: the ring only matters below an octree
+    // level's root, for octree levels deeper than the ring
+    int deepest = 0;
+    for (const Level& L : V.spec.lv)
+        if (L.kind == K_SVO || L.kind == K_DAG) deepest = std::max(deepest, L.e[0]);
+    for (int d : {1, 2, 4}) {
+        if (d + 1 >= deepest || cur.restart) break;
+        vx_trace_opts c = cur;
+        c.short_stack = d;
+        consider(c);
+    }
     // staging applies to a Raw / DF top level of at most 8192 words
     {
         const Level& L0 = V.spec.lv[0];
         const uint64_t words = (1ull << (L0.e[0] + L0.e[1] + L0.e[2])) * (L0.kind == K_DF ? 2u : 1u);
-        if ((L0.kind == K_RAW || L0.kind == K_DF) && words <= 8192 && !cur.restart) {
+        if ((L0.kind == K_RAW || L0.kind == K_DF) && words <= 8192 && !cur.restart && !cur.short_stack) {
             vx_trace_opts c = cur;
             c.smem_top = 1;
             consider(c);

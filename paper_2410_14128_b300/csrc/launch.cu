@@ -185,6 +185,8 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PERSISTENT;
     const int sort = o ? o->sort_cell_log2 : 0;
     const int restart = o ? o->restart : 0;
+    // the walker's resume mode: full node stack, restarting traversal, or a short stack of depth D
+    const int stack = restart ? -1 : (o ? o->short_stack : 0);
     cudaStream_t st = (cudaStream_t)stream;
     // Optional coherence sort: scratch from the stream-ordered pool, freed
     // on the same stream after the trace.
@@ -214,10 +216,10 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int bps = o ? o->blocks_per_sm : 0;
         const int smem_top = o ? o->smem_top : 0;
         e = v.kernels->trace_persistent(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits,
-                                        layout, block, bps, refill, burst, restart, smem_top, st, next);
+                                        layout, block, bps, refill, burst, stack, smem_top, st, next);
     } else {
         e = v.kernels->trace(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits, layout,
-                             block, restart, st);
+                             block, stack, st);
     }
     if (scratch) cudaFreeAsync(scratch, st);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));
@@ -316,19 +318,25 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         g->d.start[k + 1] = g->d.start[k] + it.n;
     }
     if (subs.empty()) return VX_OK;
-    // Options: explicit ones, else the first volume's tuned persistent-mode
-    // settings, else the defaults (plain-mode tunings do not carry over).
-    vx_trace_opts def{};
-    if (!o || o->mode == VX_MODE_AUTO) {
-        Volume& mv = const_cast<Volume&>(*subs[0].v0);
-        std::lock_guard<std::mutex> lock(mv.tune_mu);
-        if (mv.tuned && mv.tuned_opts.mode == VX_MODE_PERSISTENT) def = mv.tuned_opts;
-    } else {
-        def = *o;
+    // Options of each group: explicit ones, else its volume's tuned
+    // persistent-mode block, refill and burst (its own format's best), else
+    // the defaults (plain-mode tunings do not carry over).
+    const int nsub = (int)subs.size();
+    std::vector<vx_trace_opts> gopts(nsub);
+    for (int i = 0; i < nsub; i++) {
+        vx_trace_opts def{};
+        if (!o || o->mode == VX_MODE_AUTO) {
+            Volume& mv = const_cast<Volume&>(*subs[i].v0);
+            std::lock_guard<std::mutex> lock(mv.tune_mu);
+            if (mv.tuned && mv.tuned_opts.mode == VX_MODE_PERSISTENT) def = mv.tuned_opts;
+        } else {
+            def = *o;
+        }
+        if (def.block <= 0) def.block = 256;
+        if (def.refill <= 0) def.refill = kDefaultRefill;
+        if (def.burst <= 0) def.burst = kDefaultBurst;
+        gopts[i] = def;
     }
-    const int block = def.block > 0 ? def.block : 256;
-    const int refill = def.refill > 0 ? def.refill : kDefaultRefill;
-    const int burst = def.burst > 0 ? def.burst : kDefaultBurst;
 
     std::lock_guard<std::mutex> lock(g_fork_mu);
     DevStreams& F = g_fork[dev];
@@ -342,7 +350,6 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (e) return fail(VX_ECUDA, "batch events: %s", cudaGetErrorString(e));
         F.ready = true;
     }
-    const int nsub = (int)subs.size();
     // Grid of every group, decided before anything is enqueued: a failure
     // here leaves no forked stream behind.
     // Every launch gets a full GPU's worth of resident blocks: the launches
@@ -357,6 +364,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (!nexts[i])
             return fail(VX_EUNSUPPORTED, "no queue counter for the batched kernel (at most %d captured "
                         "persistent launches per volume)", kQueueCaptured);
+        const int block = gopts[i].block;
         int per_sm = 1;
         int rc = g.ks->resident_blocks(g.v0->spec.fmt, layout, block, &per_sm);
         if (rc) return fail(VX_ECUDA, "occupancy: %s", cudaGetErrorString((cudaError_t)rc));
@@ -385,7 +393,8 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
             rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
             break;
         }
-        int lr = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, block, grids[i], refill, burst, fs, nexts[i]);
+        const vx_trace_opts& go = gopts[i];
+        int lr = g.ks->trace_batch(g.v0->spec.fmt, g.d, layout, go.block, grids[i], go.refill, go.burst, fs, nexts[i]);
         if (lr) {
             rc = fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)lr));
             break;

@@ -80,13 +80,23 @@ struct StatF {
     static constexpr int kMaxJ = (int)J_;
     __device__ __forceinline__ int J() const { return (int)J_; }
     __device__ __forceinline__ int kind(int j) const { return (int)((KIND >> (2 * j)) & 3u); }
-    __device__ __forceinline__ int s(int j) const { return (int)((S >> (4 * j)) & 15u); }
-    __device__ __forceinline__ int b(int j) const { return (int)((B >> (4 * j)) & 15u); }
+    // 4-bit fields of the packed 64-bit constants; a 32-bit shift when the
+    // fields a walk can index fit the low word (J <= 8 node levels, grids of
+    // at most 2^8 per axis for jpop), a 64-bit funnel shift otherwise
+    __device__ __forceinline__ int s(int j) const {
+        return J_ <= 8 ? (int)(((uint32_t)S >> (4 * j)) & 15u) : (int)((S >> (4 * j)) & 15u);
+    }
+    __device__ __forceinline__ int b(int j) const {
+        return J_ <= 8 ? (int)(((uint32_t)B >> (4 * j)) & 15u) : (int)((B >> (4 * j)) & 15u);
+    }
     __device__ __forceinline__ bool bot(int j) const { return (BOT >> j) & 1u; }
     __device__ __forceinline__ uint32_t top() const { return TOP; }
     __device__ __forceinline__ int b0(int a) const { return (int)(a == 0 ? B0X : (a == 1 ? B0Y : B0Z)); }
     __device__ __forceinline__ int ldim(int a) const { return (int)(a == 0 ? LX : (a == 1 ? LY : LZ)); }
-    __device__ __forceinline__ int jpop(int h) const { return (int)((JPOP >> (4 * h)) & 15u); }
+    __device__ __forceinline__ int jpop(int h) const {
+        constexpr uint32_t kMaxL = LX > LY ? (LX > LZ ? LX : LZ) : (LY > LZ ? LY : LZ);
+        return kMaxL <= 8 ? (int)(((uint32_t)JPOP >> (4 * h)) & 15u) : (int)((JPOP >> (4 * h)) & 15u);
+    }
     static constexpr bool kHasSvo = (KIND & 0x55555555u & ~(KIND >> 1)) != 0;
     static constexpr bool kHasDag = ((KIND >> 1) & 0x55555555u & ~KIND) != 0;
     static constexpr bool kHasDf = (KIND & (KIND >> 1) & 0x55555555u) != 0;
@@ -292,10 +302,16 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // level, one 8-byte entry per level, and the start voxel) lives in the
 // kernel's dynamic shared memory (vx_dyn_smem below), one column per thread.
 //
-// RESTART selects the paper's restarting sparse-voxel intersection (Sec.
-// 4.4): only the root node of each format level is kept; leaving a node of
-// an SVO or SVDAG level walks that level's octree again from its root down
-// to the resuming node level, at the price of re-reading those nodes.
+// SMODE selects how nodes are resumed after a step leaves a node:
+//   0  full stack: one entry per node level, every node entered is kept;
+//   1  the paper's restarting sparse-voxel intersection (Sec. 4.4): only the
+//      root node of each format level is kept; leaving a node of an SVO or
+//      SVDAG level walks that level's octree again from its root down to the
+//      resuming node level, at the price of re-reading those nodes;
+//   2  short stack: the format levels' roots, plus the nodes of the other
+//      (octree) node levels in a ring of D = sdm + 1 entries indexed by
+//      j mod D and tagged with their level; a pop whose entry was overwritten
+//      by a deeper level falls back to the restart of mode 1.
 //
 // TOPS: the cells of node level 0 (a Raw or DF top level) were copied into
 // shared memory by the calling kernel (after the node stacks), and level-0
@@ -320,11 +336,15 @@ void prefer_carveout(const void* kernel, size_t smem_per_block, int block);
 
 // Entries per thread: one {pointer, valid mask} per node level, then two
 // holding the ray's start voxel; the stride rounds that up to an odd count.
-__host__ __device__ constexpr uint32_t stack_entries(uint32_t J) { return J + 2u; }
-__host__ __device__ constexpr uint32_t stack_stride(uint32_t J) { return stack_entries(J) | 1u; }
-inline size_t stack_bytes(uint32_t J, int block) { return (size_t)stack_stride(J) * (size_t)block * sizeof(uint2); }
+// A short stack (mode 2) adds its ring of D entries after those.
+__host__ __device__ constexpr uint32_t stack_entries(uint32_t J, uint32_t D = 0) { return J + 2u + D; }
+__host__ __device__ constexpr uint32_t stack_stride(uint32_t J, uint32_t D = 0) { return stack_entries(J, D) | 1u; }
+inline size_t stack_bytes(uint32_t J, int block, uint32_t D = 0) {
+    return (size_t)stack_stride(J, D) * (size_t)block * sizeof(uint2);
+}
+constexpr int kShortStackMax = 8;  // ring depths 1, 2, 4, 8
 
-template <bool COUNT, class F, bool RESTART = false, bool TOPS = false>
+template <bool COUNT, class F, int SMODE = 0, bool TOPS = false>
 struct Walker {
     RayIn r;
     float inv[3];
@@ -338,6 +358,7 @@ struct Walker {
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
     uint32_t sb;      // shared-window byte address of this thread's stack entry 0
+    uint32_t sdm = 0;  // short stack (SMODE 2): ring depth - 1, a power of two minus one
     uint32_t lim;     // words in the image (checked by the instrumented walker)
     uint32_t* sect;   // instrumented walker: one bit per 32-byte sector of the image it read, or null
     Cnt cnt;
@@ -378,12 +399,13 @@ struct Walker {
     // pops to jpop(h) <= j); the instrumented walker also checks it and
     // refuses an access outside it (counted like a refused read).
     __device__ __forceinline__ uint32_t saddr(const F& f, int e) {
-        if (COUNT && (unsigned)e >= stack_entries((uint32_t)f.J())) {
+        if (COUNT && (unsigned)e >= stack_entries((uint32_t)f.J(), ring())) {
             cnt.refused++;
             e = 0;
         }
         return sb + 8u * (uint32_t)e;
     }
+    __device__ __forceinline__ uint32_t ring() const { return SMODE == 2 ? sdm + 1u : 0u; }
     __device__ __forceinline__ uint2 sget(const F& f, int e) {
         uint2 v;
         asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr(f, e)));
@@ -393,7 +415,7 @@ struct Walker {
         asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(saddr(f, e)), "r"(v.x), "r"(v.y) : "memory");
     }
     __device__ __forceinline__ const uint32_t* top_words_smem(const F& f) const {
-        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J()) * blockDim.x);
+        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J(), ring()) * blockDim.x);
     }
 
     // Node level j: kind, children side (log2 voxels), fanout per axis, and
@@ -447,7 +469,7 @@ struct Walker {
     __device__ __forceinline__ bool start(const F& f, const Img im, const RayIn& ray, HitRec& out) {
         const uint32_t* __restrict__ pool = im.w;
         lim = im.n;
-        sb = (uint32_t)__cvta_generic_to_shared(vx_dyn_smem) + 8u * stack_stride((uint32_t)f.J()) * threadIdx.x;
+        sb = (uint32_t)__cvta_generic_to_shared(vx_dyn_smem) + 8u * stack_stride((uint32_t)f.J(), ring()) * threadIdx.x;
         r = ray;
         // Invalid rays: any NaN, or an infinite tmin.
         if (isnan(r.o[0]) || isnan(r.o[1]) || isnan(r.o[2]) || isnan(r.d[0]) || isnan(r.d[1]) || isnan(r.d[2]) ||
@@ -646,8 +668,16 @@ struct Walker {
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] >>= sh;
             j = jp;
-            if (RESTART) {
+            if (SMODE == 1) {
                 restart(f, im);
+            } else if (SMODE == 2 && !((f.top() >> j) & 1u)) {
+                const uint2 e = sget(f, f.J() + 2 + (j & (int)sdm));
+                if ((e.y >> 8) == (uint32_t)(j + 1)) {
+                    Pc = e.x;
+                    Mc = e.y & 0xFFu;
+                } else {
+                    restart(f, im);  // overwritten by a deeper level of the ring
+                }
             } else {
                 const uint2 e = sget(f, j);
                 Pc = e.x;
@@ -740,7 +770,8 @@ struct Walker {
                 else { Pn = term; Mn = rd(pool, term) & 0xFFu; VX_CNT(bytes, 4); }
             }
             ++j;
-            if (!RESTART || ((f.top() >> j) & 1u)) sput(f, j, make_uint2(Pn, Mn));
+            if (SMODE == 0 || ((f.top() >> j) & 1u)) sput(f, j, make_uint2(Pn, Mn));
+            else if (SMODE == 2) sput(f, J + 2 + (j & (int)sdm), make_uint2(Pn, Mn | ((uint32_t)(j + 1) << 8)));
             Pc = Pn;
             Mc = Mn;
             const int sn = ls(f), bn = lb(f, 0);
@@ -785,11 +816,12 @@ struct Walker {
 };
 #undef VX_CNT
 
-template <bool COUNT, class F, bool RESTART = false>
+template <bool COUNT, class F, int SMODE = 0>
 __device__ __forceinline__ HitRec trace_ray(const F& f, const Img pool, const RayIn& r, Cnt& cnt,
-                                            uint32_t* sect = nullptr) {
-    Walker<COUNT, F, RESTART> w;  // node stack in the kernel's dynamic shared memory
+                                            uint32_t* sect = nullptr, uint32_t sdm = 0) {
+    Walker<COUNT, F, SMODE> w;  // node stack in the kernel's dynamic shared memory
     w.sect = sect;
+    w.sdm = sdm;
     HitRec h;
     if (!w.start(f, pool, r, h))
         while (!w.step(f, pool, h)) {
@@ -864,16 +896,16 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // ---------------------------------------------------------------------------
 // `order` (optional): launch slot k traces ray order[k] and writes its hit
 // at order[k] (rays sorted for coherence, results in the caller's order).
-template <class F, int LAYOUT, bool RS = false>
+template <class F, int LAYOUT, int SM = 0>
 __global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __restrict__ rays,
                                                const uint32_t* __restrict__ order, uint64_t n,
-                                               void* __restrict__ hits) {
+                                               void* __restrict__ hits, uint32_t sdm) {
     const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const uint64_t i = order ? (uint64_t)__ldg(order + k) : k;
     const RayIn r = load_ray(rays, i);
     Cnt cnt;
-    const HitRec h = trace_ray<false, F, RS>(f, pool, r, cnt);
+    const HitRec h = trace_ray<false, F, SM>(f, pool, r, cnt, nullptr, sdm);
     store_hit<LAYOUT>(f, hits, i, h);
 }
 
@@ -890,7 +922,7 @@ __global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
     Cnt cnt;
     if (i < n) {
         const RayIn r = load_ray(rays, i);
-        const HitRec h = trace_ray<true, F, RS>(f, pool, r, cnt, sectors);
+        const HitRec h = trace_ray<true, F, RS ? 1 : 0>(f, pool, r, cnt, sectors);
         store_hit<LAYOUT>(f, hits, i, h);
     }
     unsigned long long b = cnt.bytes, it = cnt.iters, d = cnt.fp64, rf = cnt.refused;
@@ -967,22 +999,24 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // level 0, at most kTopSmemMaxWords) into shared memory, after the node
 // stacks; the launch provides stack_bytes(J, block) + 4 top_words bytes of
 // dynamic shared memory.
-template <class F, int LAYOUT, bool RS = false, bool TS = false>
+template <class F, int LAYOUT, int SM = 0, bool TS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
                                                           const uint32_t* __restrict__ order, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
-                                                          int refill, int burst, uint32_t top_words) {
+                                                          int refill, int burst, uint32_t top_words,
+                                                          uint32_t sdm) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (TS) {
-        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J()) * blockDim.x);
+        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J(), 0) * blockDim.x);
         const uint32_t root = ldw(pool.w, 0);
         if (root != 0)
             for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) top[i] = ldw(pool.w, root + i);
         __syncthreads();
     }
-    Walker<false, F, RS, TS> w;  // node stack in the kernel's dynamic shared memory
+    Walker<false, F, SM, TS> w;  // node stack in the kernel's dynamic shared memory
+    w.sdm = sdm;
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -1123,8 +1157,9 @@ struct KernelSet {
     const char* spec;
     bool specialized;
     FmtParams params;
+    // stack: 0 full node stack, -1 restarting traversal (Sec. 4.4), D in {1, 2, 4, 8}: short stack of depth D
     int (*trace)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
-                 void* hits, int layout, int block, int restart, cudaStream_t st);
+                 void* hits, int layout, int block, int stack, cudaStream_t st);
     int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
@@ -1132,7 +1167,7 @@ struct KernelSet {
                        uint32_t* sectors);
     int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
-                            int restart, int smem_top, cudaStream_t st, unsigned long long* next);
+                            int stack, int smem_top, cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
     int (*trace_batch)(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill, int burst,
                        cudaStream_t st, unsigned long long* next);
@@ -1145,20 +1180,24 @@ struct KernelSet {
 template <class F>
 struct Launch {
     static F make(const FmtParams& p);
-    static int trace(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
-                     void* hits, int layout, int block, int restart, cudaStream_t st) {
-        if (n == 0) return 0;
+    template <int SM>
+    static int trace_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+                        void* hits, int layout, int block, uint32_t depth, cudaStream_t st) {
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
-        const size_t sm = stack_bytes(p.J, block);
-        prefer_carveout(layout == 0 ? (restart ? (const void*)k_trace<F, 0, true> : (const void*)k_trace<F, 0, false>)
-                                    : (restart ? (const void*)k_trace<F, 1, true> : (const void*)k_trace<F, 1, false>),
-                        sm, block);
-        if (layout == 0 && !restart) k_trace<F, 0, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else if (layout == 0) k_trace<F, 0, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else if (!restart) k_trace<F, 1, false><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
-        else k_trace<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits);
+        const size_t sm = stack_bytes(p.J, block, depth);
+        const uint32_t sdm = depth ? depth - 1u : 0u;
+        prefer_carveout(layout == 0 ? (const void*)k_trace<F, 0, SM> : (const void*)k_trace<F, 1, SM>, sm, block);
+        if (layout == 0) k_trace<F, 0, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits, sdm);
+        else k_trace<F, 1, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits, sdm);
         return (int)cudaGetLastError();
+    }
+    static int trace(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+                     void* hits, int layout, int block, int stack, cudaStream_t st) {
+        if (n == 0) return 0;
+        if (stack < 0) return trace_as<1>(p, pool, rays, order, n, hits, layout, block, 0, st);
+        if (stack > 0) return trace_as<2>(p, pool, rays, order, n, hits, layout, block, (uint32_t)stack, st);
+        return trace_as<0>(p, pool, rays, order, n, hits, layout, block, 0, st);
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                            int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
@@ -1185,31 +1224,32 @@ struct Launch {
         const uint64_t words = cells * (k0 == K_DF ? 2u : 1u);
         return words <= kTopSmemMaxWords ? (uint32_t)words : 0u;
     }
-    template <bool RS, bool TS>
+    template <int SM, bool TS>
     static int persistent_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                              uint64_t n, void* hits, int layout, int block, int per_sm_req, int refill, int burst,
-                             cudaStream_t st, unsigned long long* next, uint32_t tw) {
+                             cudaStream_t st, unsigned long long* next, uint32_t tw, uint32_t depth = 0) {
         const F f = make(p);
         int dev = 0, sms = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e) return (int)e;
-        const size_t smem = stack_bytes(p.J, block) + (TS ? (size_t)tw * sizeof(uint32_t) : 0);
+        const size_t smem = stack_bytes(p.J, block, depth) + (TS ? (size_t)tw * sizeof(uint32_t) : 0);
+        const uint32_t sdm = depth ? depth - 1u : 0u;
         if (TS && smem > 48 * 1024) {  // above the default limit of dynamic shared memory
-            e = layout == 0 ? cudaFuncSetAttribute(k_trace_persistent<F, 0, RS, TS>,
+            e = layout == 0 ? cudaFuncSetAttribute(k_trace_persistent<F, 0, SM, TS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(k_trace_persistent<F, 1, RS, TS>,
+                            : cudaFuncSetAttribute(k_trace_persistent<F, 1, SM, TS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e) return (int)e;
         }
-        prefer_carveout(layout == 0 ? (const void*)k_trace_persistent<F, 0, RS, TS>
-                                    : (const void*)k_trace_persistent<F, 1, RS, TS>,
+        prefer_carveout(layout == 0 ? (const void*)k_trace_persistent<F, 0, SM, TS>
+                                    : (const void*)k_trace_persistent<F, 1, SM, TS>,
                         smem, block);
         int per_sm = per_sm_req;
         if (per_sm <= 0) {
             e = layout == 0
-                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, RS, TS>, block, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, RS, TS>, block, smem);
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 0, SM, TS>, block, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_persistent<F, 1, SM, TS>, block, smem);
             if (e) return (int)e;
             if (per_sm < 1) per_sm = 1;
         }
@@ -1220,27 +1260,33 @@ struct Launch {
         if (e) return (int)e;
         const unsigned g = (unsigned)grid;
         if (layout == 0)
-            k_trace_persistent<F, 0, RS, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw);
+            k_trace_persistent<F, 0, SM, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw,
+                                                                    sdm);
         else
-            k_trace_persistent<F, 1, RS, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw);
+            k_trace_persistent<F, 1, SM, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw,
+                                                                    sdm);
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
     // smem_top: stage a Raw / DF top level of at most kTopSmemMaxWords words in
-    // shared memory (ignored for other formats; not combined with restart).
+    // shared memory (ignored for other formats; not combined with restart or
+    // a short stack).
     static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
-                                int burst, int restart, int smem_top, cudaStream_t st, unsigned long long* next) {
+                                int burst, int stack, int smem_top, cudaStream_t st, unsigned long long* next) {
         if (n == 0) return 0;
         const uint32_t tw = top_words(p);
-        if (restart)
-            return persistent_as<true, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
-                                              burst, st, next, 0);
-        if (smem_top && tw)
-            return persistent_as<false, true>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
-                                              burst, st, next, tw);
-        return persistent_as<false, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+        if (stack < 0)
+            return persistent_as<1, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0);
+        if (stack > 0)
+            return persistent_as<2, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                           burst, st, next, 0, (uint32_t)stack);
+        if (smem_top && tw)
+            return persistent_as<0, true>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                          burst, st, next, tw);
+        return persistent_as<0, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+                                       burst, st, next, 0);
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {
         const size_t sm = stack_bytes(p.J, block);

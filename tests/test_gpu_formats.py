@@ -10,9 +10,11 @@ size, and checks:
     outside near-ties, hit t within 1e-5 relative);
   - that every launch configuration the autotuner can choose (plain and
     persistent kernels, block sizes, refill settings, coherence sort, top level
-    in shared memory, the restarting traversal of Sec. 4.4, the batched kernel,
-    the instrumented kernel) and the kernels that read the format at run time
-    return bit-identical hit records on all rays;
+    in shared memory, the restarting traversal of Sec. 4.4, short stacks of
+    depth 1, 2 and 4 with restart on overflow, the batched kernel, the
+    instrumented kernel), the kernels that read the format at run time and
+    the canonical (unaligned, unpacked) device image return bit-identical hit
+    records on all rays;
   - that the pinhole render kernel returns the same records as a trace of the
     same camera's rays.
 
@@ -85,6 +87,9 @@ def _variants(vol, gen, canon):
         ("persistent block 128 refill 1 burst 16", vol, dict(mode=Q, block=128, refill=1, burst=16)),
         ("persistent block 64 refill 32 burst 1", vol, dict(mode=Q, block=64, refill=32, burst=1)),
         ("persistent restart", vol, dict(mode=Q, restart=True)),
+        ("persistent short stack 1", vol, dict(mode=Q, short_stack=1)),
+        ("plain short stack 2", vol, dict(mode=P, short_stack=2)),
+        ("persistent short stack 4", vol, dict(mode=Q, short_stack=4)),
         ("plain restart", vol, dict(mode=P, restart=True)),
         ("persistent sorted g4", vol, dict(mode=Q, sort=4)),
         ("plain sorted g5", vol, dict(mode=P, sort=5)),
