@@ -334,10 +334,12 @@ constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB: R(4,4,4) or D(4,4,4,M)
 // (launch.cu).
 void prefer_carveout(const void* kernel, size_t smem_per_block, int block);
 
-// Entries per thread: one {pointer, valid mask} per node level, then two
-// holding the ray's start voxel; the stride rounds that up to an odd count.
-// A short stack (mode 2) adds its ring of D entries after those.
-__host__ __device__ constexpr uint32_t stack_entries(uint32_t J, uint32_t D = 0) { return J + 2u + D; }
+// Entries per thread: one {pointer, valid mask} per node level, then three
+// holding values a walk reads rarely -- {start voxel x, y}, {start voxel z,
+// tmax}, {position guard band, unused} -- which would otherwise take
+// registers; the stride rounds that up to an odd count.  A short stack
+// (mode 2) adds its ring of D entries after those.
+__host__ __device__ constexpr uint32_t stack_entries(uint32_t J, uint32_t D = 0) { return J + 3u + D; }
 __host__ __device__ constexpr uint32_t stack_stride(uint32_t J, uint32_t D = 0) { return stack_entries(J, D) | 1u; }
 inline size_t stack_bytes(uint32_t J, int block, uint32_t D = 0) {
     return (size_t)stack_stride(J, D) * (size_t)block * sizeof(uint2);
@@ -350,10 +352,9 @@ struct Walker {
     float inv[3];
     float tx, tcur;
     float gabs;  // guard band: 2^-20 of the largest |t| this walk compares
-    float gpos;  // guard band for positions o + t d inside the grid
     // (direction sign per axis, -1 / 0 / 1: sgn(), from the ray)
     int c[3];  // cell at node level j (the start voxel is kept in the stack array)
-    int j, la, lp, budget;
+    int j, la, budget;
     int skip;  // DF level: cells the walk may still enter without a look-up
     bool fresh;
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
@@ -394,7 +395,7 @@ struct Walker {
 
 
     // Node-stack entry e of this thread (0 <= e < stack_entries(J); entries
-    // J and J + 1 hold the start voxel).  Every index the walk forms lies in
+    // J .. J + 2 hold the start voxel, tmax and the position guard band).  Every index the walk forms lies in
     // that range by construction (j only grows by descents below J - 1 and
     // pops to jpop(h) <= j); the instrumented walker also checks it and
     // refuses an access outside it (counted like a refused read).
@@ -560,7 +561,7 @@ struct Walker {
         // by the FP64 tie rule: it lives in the stack's two extra entries,
         // not in registers
         sput(f, f.J(), make_uint2((uint32_t)v0l[0], (uint32_t)v0l[1]));
-        sput(f, f.J() + 1, make_uint2((uint32_t)v0l[2], 0u));
+        sput(f, f.J() + 1, make_uint2((uint32_t)v0l[2], __float_as_uint(r.tmax)));
 
         // ---- root node ----
         const uint32_t root = rd(pool, 0);
@@ -583,9 +584,8 @@ struct Walker {
 #pragma unroll
             for (int i = 0; i < 3; i++) c[i] = v0l[i] >> s0;
         }
-        la = ea;                                                        // axis of the last crossing
+        la = ea;  // axis of the last crossing
         tcur = te;
-        lp = ea >= 0 ? (sgn(ea) > 0 ? 0 : (1 << f.ldim(ea))) : 0;  // its plane
         fresh = true;  // no step taken yet
         // Every crossing this walk compares lies in [min(te, tx), max(te, tx)]
         // (crossings past the exit end it), and the FP32 error of one is at
@@ -593,8 +593,10 @@ struct Walker {
         gabs = kGuard * fmaxf(fabsf(te), fabsf(tx));
         // o + t d (FP32) is off by at most |d| 3 2^-24 |t| + 2^-24 |p|, with
         // |t| <= max(|te|, |tx|) and |p| within the grid where it matters.
-        gpos = gabs * fmaxf(fabsf(r.d[0]), fmaxf(fabsf(r.d[1]), fabsf(r.d[2]))) +
-               kGuard * (float)(2 << max(f.ldim(0), max(f.ldim(1), f.ldim(2))));
+        // (read by descents only: kept in the thread's shared-memory entries)
+        const float gpos = gabs * fmaxf(fabsf(r.d[0]), fmaxf(fabsf(r.d[1]), fabsf(r.d[2]))) +
+                           kGuard * (float)(2 << max(f.ldim(0), max(f.ldim(1), f.ldim(2))));
+        sput(f, f.J() + 2, make_uint2(__float_as_uint(gpos), 0u));
         // A ray crosses at most nx + ny + nz cells of any level and each step
         // costs at most J descents; past this bound the ray reports ST_ERROR.
         budget = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (f.J() + 2);
@@ -636,7 +638,8 @@ struct Walker {
         if (!out_now) {
             if (near(tm, tx)) {
                 VX_CNT(fp64, 1);
-                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], r.tmax, f.ldim(0), f.ldim(1),
+                const float tmax = __uint_as_float(sget(f, f.J() + 1).y);
+                out_now = exits64(r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2], tmax, f.ldim(0), f.ldim(1),
                                   f.ldim(2), sel3(r.o, a), sel3(r.d, a), pla);
             } else {
                 out_now = !(tm < tx);
@@ -653,7 +656,6 @@ struct Walker {
             if (i == a) c[i] = nw;
         tcur = tm;
         la = a;
-        lp = pla;
         fresh = false;
         const int h = 31 - __clz((uint32_t)(old ^ nw)) + ls(f);  // highest changed voxel-coordinate bit
         const int span = j == 0 ? f.ldim(a) : f.s(j - 1);
@@ -671,7 +673,7 @@ struct Walker {
             if (SMODE == 1) {
                 restart(f, im);
             } else if (SMODE == 2 && !((f.top() >> j) & 1u)) {
-                const uint2 e = sget(f, f.J() + 2 + (j & (int)sdm));
+                const uint2 e = sget(f, f.J() + 3 + (j & (int)sdm));
                 if ((e.y >> 8) == (uint32_t)(j + 1)) {
                     Pc = e.x;
                     Mc = e.y & 0xFFu;
@@ -771,7 +773,7 @@ struct Walker {
             }
             ++j;
             if (SMODE == 0 || ((f.top() >> j) & 1u)) sput(f, j, make_uint2(Pn, Mn));
-            else if (SMODE == 2) sput(f, J + 2 + (j & (int)sdm), make_uint2(Pn, Mn | ((uint32_t)(j + 1) << 8)));
+            else if (SMODE == 2) sput(f, J + 3 + (j & (int)sdm), make_uint2(Pn, Mn | ((uint32_t)(j + 1) << 8)));
             Pc = Pn;
             Mc = Mn;
             const int sn = ls(f), bn = lb(f, 0);
@@ -793,10 +795,16 @@ struct Walker {
                 const float q = p * scale;
                 int cn = (int)fminf(fmaxf(floorf(q), (float)base), (float)topc);
                 const float rq = rintf(q);
-                if (rq > (float)base && rq <= (float)topc && fabsf(q - rq) <= gpos * scale) {
+                if (rq > (float)base && rq <= (float)topc &&
+                    fabsf(q - rq) <= __uint_as_float(sget(f, J + 2).x) * scale) {
                     VX_CNT(fp64, 1);
                     const int B = (int)rq;
-                    const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, sel3(r.o, la), sel3(r.d, la), lp, la);
+                    // plane of the crossing that entered the parent's cell (voxel units):
+                    // the parent cell's face on axis la, from its coordinate (c[la]
+                    // already holds the child's when la < i)
+                    const int cpar = la < i ? (sel3(c, la) >> bn) : sel3(c, la);
+                    const int lpl = (cpar + (sgn(la) < 0 ? 1 : 0)) << (sn + bn);
+                    const bool cr = crossed64(r.o[i], r.d[i], B << sn, i, sel3(r.o, la), sel3(r.d, la), lpl, la);
                     cn = sgn(i) > 0 ? (cr ? B : B - 1) : (cr ? B - 1 : B);
                     // a ray that started on plane B took the start voxel's
                     // convention; a crossing at that same instant must not undo it
@@ -1080,8 +1088,9 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
     int set = 0;
-    Img pool{nullptr, desc.packed, 0xFFFFFFFFu, desc.aligned};
-    void* hits = nullptr;
+    // a lane's image and hit array are looked up by its set in the
+    // descriptor (kernel parameters) when used, not held in registers
+    auto img = [&]() { return Img{desc.pool[set], desc.packed, 0xFFFFFFFFu, desc.aligned}; };
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
         if (exhausted) {
@@ -1104,10 +1113,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
                     }
                     set = lo;
                     idx = slot - desc.start[set];
-                    pool.w = desc.pool[set];
-                    hits = desc.hits[set];
                     HitRec h;
-                    if (w.start(f, pool, load_ray(desc.rays[set], idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
+                    if (w.start(f, img(), load_ray(desc.rays[set], idx), h)) store_hit<LAYOUT>(f, desc.hits[set], idx, h);
                     else live = true;
                 }
             }
@@ -1116,8 +1123,8 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
         if (live) {
             for (int k = 0; k < burst; k++) {
                 HitRec h;
-                if (w.step(f, pool, h)) {
-                    store_hit<LAYOUT>(f, hits, idx, h);
+                if (w.step(f, img(), h)) {
+                    store_hit<LAYOUT>(f, desc.hits[set], idx, h);
                     live = false;
                     break;
                 }
