@@ -531,6 +531,21 @@ def run_headline(args):
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     ok_same = ok_same and all(torch.equal(h, r) for (_, _, h), r in zip(sets, ref))
     del graphs
+    # each group's kernel alone (its 16 sets in one uncaptured call), for the
+    # kernel's own speed: inside the step it shares the SMs with the others
+    group_alone_ms = []
+    for k in range(n_groups):
+        own = [sets[i] for i in range(k, N_SETS, len(vols))]
+        pair = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+        for e in pair:
+            e.record()
+        ts = []
+        for rep in range(6):
+            vx.trace_batch(own, events=pair)
+            torch.cuda.synchronize()
+            if rep >= 1:
+                ts.append(pair[0].elapsed_time(pair[1]))
+        group_alone_ms.append(float(np.mean(ts)))
 
     # --- roofline of the dominant kernel (the longest group) ---
     dom = int(np.argmax([np.mean(m) for m in group_ms]))
@@ -553,7 +568,10 @@ def run_headline(args):
                 "alg_bytes_per_launch": int(alg),
                 "alg_bytes_per_ray": round(alg / g_rays, 2),
                 "avg_launch_ms": round(avg_ms, 4),
+                "avg_launch_ms_alone": round(group_alone_ms[dom], 4),
+                "frac_alone": round(alg / (group_alone_ms[dom] / 1e3) / 1e9 / peak, 4),
                 "group_launch_ms": [round(float(np.mean(m)), 4) for m in group_ms],
+                "group_launch_ms_alone": [round(t, 4) for t in group_alone_ms],
                 "timing": "CUDA events recorded by vx_trace_batch_timed on each group's stream, inside the "
                           "graphs replayed in the timed region",
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}

@@ -13,6 +13,8 @@
 //     bits 24..31, which saves the dependent read of the node's masks word on
 //     every descent, and an SVDAG slot of a leaf child holds the leaf's
 //     terminating integer itself, so the leaf words are not stored at all.
+// The image has an even number of words, so a kernel may read any cell as
+// part of the 8-byte pair that starts at the even word at or below it.
 // vx_canonical keeps returning the paper's layout; canonical_device uploads
 // it unchanged (then the kernels read it with 4-byte loads).
 #include <string.h>
@@ -57,6 +59,7 @@ class Relocator {
         uint64_t size = assign(any_dag);
         packed = any_dag && size < (1ull << 24);
         if (any_dag && !packed) size = assign(false);
+        size += size & 1;  // an even number of words: every aligned 8-byte pair lies inside
         if (size > 0xFFFFFFFFull) return false;
         out.assign((size_t)size, 0u);
         out[0] = ptr_to(0, in_[0], packed);

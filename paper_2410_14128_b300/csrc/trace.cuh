@@ -723,12 +723,19 @@ struct Walker {
         if (staged) {
             if (is_raw || df_read) w = top_words_smem(f)[as];
             if (df_read) dist = top_words_smem(f)[as + 1];
-        } else if (df_read) {  // {terminating integer, distance}: one sector
-            const uint2 cell = rd2(im, a);
-            w = cell.x;
-            dist = cell.y;
-        } else if (is_raw) {
-            w = rd(pool, a);
+        } else if (!COUNT && f.has_df() && im.aligned) {
+            // one 8-byte load for lanes at DF and at Raw levels alike: a DF
+            // cell {terminating integer, distance} starts at an even word; a
+            // Raw cell is the half of its aligned pair that the parity picks
+            // (the image ends on an even word, so the pair is inside it)
+            if (is_raw || df_read) {
+                const uint2 v = __ldg(reinterpret_cast<const uint2*>(pool + (a & ~1u)));
+                w = (a & 1u) ? v.y : v.x;
+                dist = v.y;
+            }
+        } else {
+            if (is_raw || df_read) w = rd(pool, a);
+            if (df_read) dist = rd(pool, a + 1);  // same sector as the cell word
         }
         VX_CNT(bytes, is_raw ? 4 : (df_read ? 8 : 0));
         const bool occ = (is_raw || is_df) ? w != 0u : ((Mc >> idx) & 1u) != 0u;

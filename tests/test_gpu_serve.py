@@ -80,13 +80,17 @@ def test_results_same_alone_and_in_the_mix(volumes):
 
 
 def test_requests_are_admitted_while_others_run_and_overlap_on_the_gpu(volumes):
-    # continuous batching: a request that arrives while others are on the GPU
-    # is admitted as soon as memory allows, and its device work overlaps
-    # theirs (read from CUDA events on the server's streams)
+    # continuous batching: requests waiting while others are on the GPU are
+    # admitted as soon as a slot frees (here 4 slots, 40 requests queued at
+    # once), not after the queue drains, and the device work of requests on
+    # different streams overlaps (read from CUDA events on the server's streams)
     vols, grids = volumes
-    reqs = make_requests(15, 80, 0.03, grids)
-    srv = serve.Server(vols, mem_budget_bytes=8 << 20, record_device_times=True)
-    res = srv.run(reqs, realtime=True)
+    names = sorted(grids)
+    reqs = [serve.Request(i, names[i % len(names)], 0.0,
+                          camera=synth.camera(1500 + i, grids[names[i % len(names)]].shape[0], 640, 480, mode="above"))
+            for i in range(40)]
+    srv = serve.Server(vols, mem_budget_bytes=64 << 20, max_inflight=4, record_device_times=True)
+    res = srv.run(reqs, realtime=False)
     for r in reqs:
         out = res[r.id]
         assert out.refused is None
