@@ -224,10 +224,13 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *   block  threads per block: 0 = default (256; 128 for the plain render
  *          kernel), else a multiple of 32 in [32, 256] (VX_EINVAL otherwise);
  *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = as many as fit;
- *   smem_top  persistent mode: 1 = each block first copies the top level
- *          into shared memory and reads its cells there (a Raw or DF top
- *          level of at most 8192 words, without restart; ignored otherwise);
- *          0 = off.  Any other value: VX_EINVAL;
+ *   smem_top  persistent mode, staging depth: k in [1, 8] = each block first
+ *          copies the structures of the top k node levels (any level kind:
+ *          Raw, DF, SVO, SVDAG) into shared memory and reads them there; the
+ *          device image holds them as one prefix, level by level.  The
+ *          largest depth <= k whose prefix fits 8192 words (32 KiB) is used;
+ *          none for a canonical device image, with restart or with a short
+ *          stack.  0 = off.  Any other value: VX_EINVAL;
  *   refill persistent mode: a warp fetches new rays once this many of its
  *          lanes are idle (1..32), 0 = default;
  *   burst  persistent mode: loop iterations between refill checks, 0 = default;

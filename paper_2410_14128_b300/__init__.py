@@ -172,7 +172,7 @@ def _opts(mode=MODE_AUTO, block=0, blocks_per_sm=0, refill=0, burst=0, sort=0, r
 def _opts_dict(o: _TraceOpts) -> dict:
     return {"mode": {1: "plain", 2: "persistent"}.get(o.mode, o.mode), "block": o.block, "refill": o.refill,
             "burst": o.burst, "sort_cell_log2": o.sort_cell_log2, "restart": bool(o.restart),
-            "smem_top": bool(o.smem_top), "short_stack": o.short_stack}
+            "smem_top": o.smem_top, "short_stack": o.short_stack}
 
 
 def _camera(cam: dict) -> _Camera:

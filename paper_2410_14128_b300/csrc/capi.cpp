@@ -75,7 +75,8 @@ int check_opts(const vx_trace_opts* o) {
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32)
         return fail(VX_EINVAL, "blocks_per_sm must be in [0, 32], got %d", o->blocks_per_sm);
     if (o->restart != 0 && o->restart != 1) return fail(VX_EINVAL, "restart must be 0 or 1, got %d", o->restart);
-    if (o->smem_top != 0 && o->smem_top != 1) return fail(VX_EINVAL, "smem_top must be 0 or 1, got %d", o->smem_top);
+    if (o->smem_top < 0 || o->smem_top > kStageLevels)
+        return fail(VX_EINVAL, "smem_top must be in [0, %d], got %d", kStageLevels, o->smem_top);
     if (o->short_stack != 0 && o->short_stack != 1 && o->short_stack != 2 && o->short_stack != 4 &&
         o->short_stack != 8)
         return fail(VX_EINVAL, "short_stack must be 0, 1, 2, 4 or 8, got %d", o->short_stack);
@@ -168,7 +169,7 @@ int upload(Volume& V, const vx_build_opts& o, bool allow_packed) {
     V.device = dev;
     std::vector<uint32_t> image;
     bool packed = false;
-    const bool relocated = allow_packed && make_device_image(V.spec, V.built.words, image, &packed);
+    const bool relocated = allow_packed && make_device_image(V.spec, V.built.words, image, &packed, V.stage_end);
     V.packed = relocated && packed ? 1 : 0;
     V.aligned = relocated ? 1 : 0;
     const std::vector<uint32_t>& src = relocated ? image : V.built.words;
@@ -489,13 +490,16 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
         c.short_stack = d;
         consider(c);
     }
-    // staging applies to a Raw / DF top level of at most 8192 words
-    {
-        const Level& L0 = V.spec.lv[0];
-        const uint64_t words = (1ull << (L0.e[0] + L0.e[1] + L0.e[2])) * (L0.kind == K_DF ? 2u : 1u);
-        if ((L0.kind == K_RAW || L0.kind == K_DF) && words <= 8192 && !cur.restart && !cur.short_stack) {
+    // staging depth: the top k node levels in shared memory, for each k whose
+    // image prefix fits and differs from the previous one
+    if (!cur.restart && !cur.short_stack) {
+        uint32_t last = 0;
+        for (int k = 1; k <= kStageLevels; k++) {
+            const uint32_t w = stage_words(V, k);
+            if (w == 0 || w == last) continue;
+            last = w;
             vx_trace_opts c = cur;
-            c.smem_top = 1;
+            c.smem_top = k;
             consider(c);
         }
     }

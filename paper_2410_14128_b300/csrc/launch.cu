@@ -36,6 +36,21 @@ CamDev to_dev(const CameraParams& c) {
 
 Img img_of(const Volume& v) { return Img{v.d_pool, v.packed, (uint32_t)v.pool_words, v.aligned}; }
 
+}  // namespace
+
+// Image words a persistent trace stages for smem_top = k: the prefix holding
+// the top k node levels of a relocated image, at the largest k <= the one
+// asked for whose prefix fits kTopSmemMaxWords; 0 for none.
+uint32_t stage_words(const Volume& v, int k) {
+    if (!v.aligned || k <= 0) return 0;
+    if (k > kStageLevels) k = kStageLevels;
+    for (; k > 0; k--)
+        if (v.stage_end[k] <= kTopSmemMaxWords) return v.stage_end[k];
+    return 0;
+}
+
+namespace {
+
 int pick_block(const vx_trace_opts* o) {
     int b = (o && o->block > 0) ? o->block : 256;
     return b;
@@ -214,9 +229,9 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
-        const int smem_top = o ? o->smem_top : 0;
+        const uint32_t stage = stage_words(v, o ? o->smem_top : 0);
         e = v.kernels->trace_persistent(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits,
-                                        layout, block, bps, refill, burst, stack, smem_top, st, next);
+                                        layout, block, bps, refill, burst, stack, stage, st, next);
     } else {
         e = v.kernels->trace(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits, layout,
                              block, stack, st);

@@ -15,6 +15,10 @@
 //     terminating integer itself, so the leaf words are not stored at all.
 // The image has an even number of words, so a kernel may read any cell as
 // part of the 8-byte pair that starts at the even word at or below it.
+// The structures read at the top node levels come first, level by level
+// (canonical order within a level, and for everything below), so that the
+// top k node levels of any format -- Raw, DF, SVO or SVDAG -- are one prefix
+// of the image, which a kernel can stage in shared memory (stage_end).
 // vx_canonical keeps returning the paper's layout; canonical_device uploads
 // it unchanged (then the kernels read it with 4-byte loads).
 #include <string.h>
@@ -39,7 +43,16 @@ class Relocator {
   public:
     Relocator(const Spec& sp, const std::vector<uint32_t>& in) : sp_(sp), in_(in), seen_(in.size(), 0) {
         nlev_ = (int)sp.lv.size();
+        int j = 0;
+        for (int k = 0; k < nlev_; k++) {
+            j0_[k] = j;
+            j += sp.lv[k].kind == K_SVO || sp.lv[k].kind == K_DAG ? sp.lv[k].e[0] : 1;
+        }
     }
+
+    // stage_end[k] (k = 0..kStageLevels): the image's words before the
+    // first structure read at node level k or deeper
+    uint32_t stage_end[kStageLevels + 1] = {};
 
     // Builds the image; false if the buffer is not a well-formed volume of
     // the spec or an offset would not fit 32 bits (the caller then uploads
@@ -54,6 +67,12 @@ class Relocator {
         level(0, in_[0]);
         if (!ok_) return false;
         std::sort(items_.begin(), items_.end(), [](const Item& a, const Item& b) { return a.old < b.old; });
+        // placement: the structures read at node levels 0 .. kStageLevels - 1
+        // first, level by level, then the rest; canonical order within each
+        order_.resize(items_.size());
+        for (size_t i = 0; i < items_.size(); i++) order_[i] = (uint32_t)i;
+        std::stable_sort(order_.begin(), order_.end(),
+                         [&](uint32_t a, uint32_t b) { return stage(items_[a]) < stage(items_[b]); });
         bool any_dag = false;
         for (const Level& L : sp_.lv) any_dag |= L.kind == K_DAG;
         uint64_t size = assign(any_dag);
@@ -142,17 +161,31 @@ class Relocator {
         }
     }
 
-    // ---- new offsets, in canonical order; returns the image size ----
+    // node level whose walk reads the structure, capped at kStageLevels
+    int stage(const Item& it) const {
+        const int j0 = j0_[it.level];
+        int j = j0;
+        if (it.kind == I_SVO_LIST) j = j0 + it.depth - 1;          // read by its parent's descent
+        else if (it.kind == I_DAG) j = j0 + it.depth;               // its slots, at its own level
+        else if (it.kind == I_DAG_LEAF) j = j0 + it.depth - 1;      // read from a slot one level up
+        return j < kStageLevels ? j : kStageLevels;
+    }
+
+    // ---- new offsets in placement order; returns the image size ----
     uint64_t assign(bool packed) {
         newoff_.assign(items_.size(), 0u);
         uint64_t cur = 1;  // word 0: root pointer
-        for (size_t i = 0; i < items_.size(); i++) {
+        int next_stage = 0;
+        for (uint32_t i : order_) {
             const Item& it = items_[i];
+            while (next_stage <= stage(it) && next_stage <= kStageLevels)
+                stage_end[next_stage++] = (uint32_t)std::min<uint64_t>(cur, 0xFFFFFFFFull);
             if (packed && it.kind == I_DAG_LEAF) continue;  // inlined into the slots
             if (it.align == 2 && (cur & 1)) cur++;
             newoff_[i] = (uint32_t)std::min<uint64_t>(cur, 0xFFFFFFFFull);
             cur += it.len;
         }
+        while (next_stage <= kStageLevels) stage_end[next_stage++] = (uint32_t)std::min<uint64_t>(cur, 0xFFFFFFFFull);
         return cur;
     }
     uint32_t where(uint32_t old) {
@@ -223,7 +256,9 @@ class Relocator {
     const std::vector<uint32_t>& in_;
     std::vector<uint8_t> seen_;
     std::vector<Item> items_;
+    std::vector<uint32_t> order_;
     std::vector<uint32_t> newoff_;
+    int j0_[kMaxFormatLevels] = {};
     int nlev_;
     bool ok_ = true;
 };
@@ -231,7 +266,7 @@ class Relocator {
 }  // namespace
 
 bool make_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out,
-                       bool* packed) {
+                       bool* packed, uint32_t* stage_end) {
     bool pk = false;
     Relocator r(spec, canonical);
     if (!r.run(out, pk)) {
@@ -239,6 +274,8 @@ bool make_device_image(const Spec& spec, const std::vector<uint32_t>& canonical,
         return false;
     }
     *packed = pk;
+    if (stage_end)
+        for (int k = 0; k <= kStageLevels; k++) stage_end[k] = r.stage_end[k];
     return true;
 }
 

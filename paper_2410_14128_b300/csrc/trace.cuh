@@ -313,9 +313,11 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 //      j mod D and tagged with their level; a pop whose entry was overwritten
 //      by a deeper level falls back to the restart of mode 1.
 //
-// TOPS: the cells of node level 0 (a Raw or DF top level) were copied into
-// shared memory by the calling kernel (after the node stacks), and level-0
-// look-ups read them there.
+// TOPS: the calling kernel copied the first `stw` words of the device image
+// into shared memory (after the node stacks); the relocated image holds the
+// structures of its top node levels there, level by level (pack.cpp), so
+// every read below word stw -- the top k node levels of any kind -- comes
+// from shared memory.
 //
 // Dynamic shared memory of every walker kernel: first the node stacks of the
 // block's threads, entry e of thread t at vx_dyn_smem[t * stack_stride(J) +
@@ -325,7 +327,7 @@ constexpr uint32_t kPtrMask = 0x00FFFFFFu;
 // conflicts), and a thread reaches any entry from one base register plus a
 // constant; the stack takes no L1 lines from node reads.
 extern __shared__ __align__(16) uint2 vx_dyn_smem[];
-constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB: R(4,4,4) or D(4,4,4,M)
+constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB of staged image words at most
 
 // Shared-memory carveout preference of a walker kernel, in percent of the
 // SM's maximum (228 KiB): what its resident blocks need (the kernels are
@@ -360,6 +362,7 @@ struct Walker {
     uint32_t Pc, Mc;  // node of level j: pointer, valid mask
     uint32_t sb;      // shared-window byte address of this thread's stack entry 0
     uint32_t sdm = 0;  // short stack (SMODE 2): ring depth - 1, a power of two minus one
+    uint32_t stw = 0;  // TOPS: words of the image staged in shared memory
     uint32_t lim;     // words in the image (checked by the instrumented walker)
     uint32_t* sect;   // instrumented walker: one bit per 32-byte sector of the image it read, or null
     Cnt cnt;
@@ -369,6 +372,7 @@ struct Walker {
     // ray then reports ST_ERROR), so it can walk a buffer nobody validated;
     // it also marks the 32-byte sector (8 words) each accepted read falls in.
     __device__ __forceinline__ uint32_t rd(const uint32_t* __restrict__ pool, uint32_t i) {
+        if (TOPS && i < stw) return staged_words()[i];
         if (COUNT) {
             if (i >= lim) {
                 cnt.refused++;
@@ -382,6 +386,7 @@ struct Walker {
     // Words i and i + 1 of the image (an SVO node entry, a DF cell): one
     // 8-byte load when the image is aligned (i is then even), else two.
     __device__ __forceinline__ uint2 rd2(const Img& im, uint32_t i) {
+        if (TOPS && i + 1u < stw) return make_uint2(staged_words()[i], staged_words()[i + 1u]);
         if (COUNT) {
             if (i + 1u >= lim || i + 1u < i || (im.aligned && (i & 1u))) {
                 cnt.refused++;
@@ -415,9 +420,9 @@ struct Walker {
     __device__ __forceinline__ void sput(const F& f, int e, uint2 v) {
         asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(saddr(f, e)), "r"(v.x), "r"(v.y) : "memory");
     }
-    __device__ __forceinline__ const uint32_t* top_words_smem(const F& f) const {
-        return reinterpret_cast<const uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J(), ring()) * blockDim.x);
-    }
+    // the staged image words (TOPS kernels run with SMODE 0: no ring)
+    __device__ __forceinline__ const uint32_t* staged_words() const { return reinterpret_cast<const uint32_t*>(vx_dyn_smem) + 2u * sbase_words; }
+    uint32_t sbase_words = 0;  // TOPS: 8-byte entries before the staged words (stacks of the block)
 
     // Node level j: kind, children side (log2 voxels), fanout per axis, and
     // whether its children are terminating integers -- extracted from the
@@ -717,13 +722,8 @@ struct Walker {
         // are entered without reading them (Sec. 4.2).
         const bool df_read = is_df && skip <= 0;
         const uint32_t a = is_df ? Pc + 2u * idx : Pc + idx;
-        const uint32_t as = is_df ? 2u * idx : idx;  // word of the cell in a staged top level
-        const bool staged = TOPS && j == 0;
         uint32_t w = 0, dist = 0;
-        if (staged) {
-            if (is_raw || df_read) w = top_words_smem(f)[as];
-            if (df_read) dist = top_words_smem(f)[as + 1];
-        } else if (!COUNT && f.has_df() && im.aligned) {
+        if (!COUNT && !TOPS && f.has_df() && im.aligned) {
             // one 8-byte load for lanes at DF and at Raw levels alike: a DF
             // cell {terminating integer, distance} starts at an even word; a
             // Raw cell is the half of its aligned pair that the parity picks
@@ -1010,10 +1010,10 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // walking.  Each round advances every live lane by up to `burst` iterations.
 // `next` must be zero at launch; the kernel leaves it >= n.
 //
-// TS: the block first copies the top level's `top_words` words (a Raw or DF
-// level 0, at most kTopSmemMaxWords) into shared memory, after the node
-// stacks; the launch provides stack_bytes(J, block) + 4 top_words bytes of
-// dynamic shared memory.
+// TS: the block first copies the image's first `top_words` words (the top
+// node levels of a relocated image, at most kTopSmemMaxWords) into shared
+// memory, after the node stacks; the launch provides stack_bytes(J, block) +
+// 4 top_words bytes of dynamic shared memory.
 template <class F, int LAYOUT, int SM = 0, bool TS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
                                                           const float4* __restrict__ rays,
@@ -1023,15 +1023,15 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
                                                           uint32_t sdm) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (TS) {
-        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem + stack_stride((uint32_t)f.J(), 0) * blockDim.x);
-        const uint32_t root = ldw(pool.w, 0);
-        if (root != 0)
-            for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) top[i] = ldw(pool.w, root + i);
-        __syncthreads();
-    }
     Walker<false, F, SM, TS> w;  // node stack in the kernel's dynamic shared memory
     w.sdm = sdm;
+    if (TS) {
+        w.sbase_words = stack_stride((uint32_t)f.J(), 0) * blockDim.x;
+        w.stw = top_words;
+        uint32_t* top = reinterpret_cast<uint32_t*>(vx_dyn_smem) + 2u * w.sbase_words;
+        for (uint32_t i = threadIdx.x; i < top_words; i += blockDim.x) top[i] = ldw(pool.w, i);
+        __syncthreads();
+    }
     bool live = false;
     bool exhausted = false;  // warp-uniform
     uint64_t idx = 0;
@@ -1181,7 +1181,7 @@ struct KernelSet {
                        uint32_t* sectors);
     int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
-                            int stack, int smem_top, cudaStream_t st, unsigned long long* next);
+                            int stack, uint32_t stage_words, cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
     int (*trace_batch)(const FmtParams& p, const BatchDesc& d, int layout, int block, int grid, int refill, int burst,
                        cudaStream_t st, unsigned long long* next);
@@ -1230,14 +1230,6 @@ struct Launch {
             k_trace_count<F, 1, true><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, counters, sectors);
         return (int)cudaGetLastError();
     }
-    // Words of a Raw / DF top level that fits the shared-memory staging, else 0.
-    static uint32_t top_words(const FmtParams& p) {
-        const int k0 = fp_kind(p, 0);
-        if (k0 != K_RAW && k0 != K_DF) return 0;
-        const uint64_t cells = 1ull << (p.b0[0] + p.b0[1] + p.b0[2]);
-        const uint64_t words = cells * (k0 == K_DF ? 2u : 1u);
-        return words <= kTopSmemMaxWords ? (uint32_t)words : 0u;
-    }
     template <int SM, bool TS>
     static int persistent_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                              uint64_t n, void* hits, int layout, int block, int per_sm_req, int refill, int burst,
@@ -1282,21 +1274,22 @@ struct Launch {
         return (int)cudaGetLastError();
     }
     // Grid = SMs x resident blocks per SM (occupancy API when blocks_per_sm is 0).
-    // smem_top: stage a Raw / DF top level of at most kTopSmemMaxWords words in
-    // shared memory (ignored for other formats; not combined with restart or
-    // a short stack).
+    // stage_words: stage the image's first stage_words words (at most
+    // kTopSmemMaxWords; the top node levels of a relocated image) in shared
+    // memory, 0 = none (not combined with restart or a short stack).
     static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
-                                int burst, int stack, int smem_top, cudaStream_t st, unsigned long long* next) {
+                                int burst, int stack, uint32_t stage_words, cudaStream_t st,
+                                unsigned long long* next) {
         if (n == 0) return 0;
-        const uint32_t tw = top_words(p);
+        const uint32_t tw = stage_words <= kTopSmemMaxWords ? stage_words : 0u;
         if (stack < 0)
             return persistent_as<1, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0);
         if (stack > 0)
             return persistent_as<2, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0, (uint32_t)stack);
-        if (smem_top && tw)
+        if (tw)
             return persistent_as<0, true>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
                                           burst, st, next, tw);
         return persistent_as<0, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,

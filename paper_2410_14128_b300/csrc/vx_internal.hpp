@@ -91,8 +91,12 @@ int validate_canonical(const Spec& spec, const uint32_t* words, uint64_t n, Buil
 // set when SVDAG pointers also carry masks (images below 2^24 words with an
 // SVDAG level).  False when the buffer is not a well-formed volume of the
 // spec (then the canonical words are uploaded as they are).
+// stage_end (optional, kStageLevels + 1 words): stage_end[k] = the image's
+// words before the first structure read at node level k or deeper (the top
+// k node levels are the prefix [0, stage_end[k])).
+constexpr int kStageLevels = 8;
 bool make_device_image(const Spec& spec, const std::vector<uint32_t>& canonical, std::vector<uint32_t>& out,
-                       bool* packed);
+                       bool* packed, uint32_t* stage_end = nullptr);
 
 // Decodes the cube (side 2^log2s at x0,y0,z0) from a canonical buffer.
 int decode_cube(const Spec& spec, const uint32_t* words, uint64_t nwords, int64_t x0, int64_t y0, int64_t z0,
@@ -137,6 +141,7 @@ struct Volume {
     uint64_t pool_words = 0;
     int packed = 0;   // device image in the packed layout (pack.cpp)
     int aligned = 0;  // device image with two-word structures at even words (pack.cpp)
+    uint32_t stage_end[kStageLevels + 1] = {};  // prefix of the image holding the top k node levels
     bool unvalidated = false;  // loaded without validation: only the checked (counted) trace may read it
     const KernelSet* kernels = nullptr;
     std::mutex staging_mu;
@@ -157,6 +162,7 @@ struct Volume {
 };
 
 const KernelSet* kernels_for(const Spec& sp);
+uint32_t stage_words(const Volume& v, int k);  // image words staged for smem_top = k (launch.cu)
 bool kernel_set_specialized(const KernelSet* k);
 
 // Kernel registry: compile-time-composed kernels for known signatures, and

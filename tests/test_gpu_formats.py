@@ -10,7 +10,7 @@ size, and checks:
     outside near-ties, hit t within 1e-5 relative);
   - that every launch configuration the autotuner can choose (plain and
     persistent kernels, block sizes, refill settings, coherence sort, top level
-    in shared memory, the restarting traversal of Sec. 4.4, short stacks of
+    in shared memory (staging depths 1 and 3), the restarting traversal of Sec. 4.4, short stacks of
     depth 1, 2 and 4 with restart on overflow, the batched kernel, the
     instrumented kernel), the kernels that read the format at run time and
     the canonical (unaligned, unpacked) device image return bit-identical hit
@@ -94,6 +94,7 @@ def _variants(vol, gen, canon):
         ("persistent sorted g4", vol, dict(mode=Q, sort=4)),
         ("plain sorted g5", vol, dict(mode=P, sort=5)),
         ("persistent top level in shared memory", vol, dict(mode=Q, smem_top=True)),
+        ("persistent top 3 node levels in shared memory", vol, dict(mode=Q, smem_top=3)),
         ("generic persistent", gen, dict(mode=Q)),
         ("generic plain restart", gen, dict(mode=P, restart=True)),
     ]

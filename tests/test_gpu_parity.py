@@ -559,10 +559,11 @@ def test_smem_top_equals_plain(spec):
     compare(g, rays, ref)
     for block, refill, burst in [(256, 8, 4), (64, 1, 1), (128, 32, 16)]:
         for rep in range(2):
-            got = gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, smem_top=True, block=block, refill=refill, burst=burst)
+            got = gpu_trace(vol, rays, mode=vx.MODE_PERSISTENT, smem_top=1 + rep * 3, block=block, refill=refill,
+                            burst=burst)
             assert np.array_equal(got, ref), (block, refill, burst, rep)
     with pytest.raises(vx.VxError):
-        gpu_trace(vol, rays, smem_top=2)
+        gpu_trace(vol, rays, smem_top=9)
 
 
 # ---------------------------------------------------------------------------

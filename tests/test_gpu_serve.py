@@ -81,15 +81,18 @@ def test_results_same_alone_and_in_the_mix(volumes):
 
 def test_requests_are_admitted_while_others_run_and_overlap_on_the_gpu(volumes):
     # continuous batching: requests waiting while others are on the GPU are
-    # admitted as soon as a slot frees (here 4 slots, 40 requests queued at
-    # once), not after the queue drains, and the device work of requests on
-    # different streams overlaps (read from CUDA events on the server's streams)
+    # admitted as soon as a slot frees (here 4 slots, 24 full-HD renders
+    # queued at once, each long enough on the GPU that the host loop sees one
+    # finish while others still run), not after the queue drains, and the
+    # device work of requests on different streams overlaps (read from CUDA
+    # events on the server's streams)
     vols, grids = volumes
     names = sorted(grids)
     reqs = [serve.Request(i, names[i % len(names)], 0.0,
-                          camera=synth.camera(1500 + i, grids[names[i % len(names)]].shape[0], 640, 480, mode="above"))
-            for i in range(40)]
-    srv = serve.Server(vols, mem_budget_bytes=64 << 20, max_inflight=4, record_device_times=True)
+                          camera=synth.camera(1500 + i, grids[names[i % len(names)]].shape[0], 1920, 1080,
+                                              mode="above"))
+            for i in range(24)]
+    srv = serve.Server(vols, mem_budget_bytes=256 << 20, max_inflight=4, record_device_times=True)
     res = srv.run(reqs, realtime=False)
     for r in reqs:
         out = res[r.id]
