@@ -142,12 +142,13 @@ NOMINAL_HBM_GBS = 8000.0  # B300 HBM3e, nominal (the measured copy rate is the r
 def trace_launches(opts: dict | None, log2_dim) -> int:
     """Kernels one vx_trace call launches: the trace, plus the coherence sort
     when the options ask for it (key histogram, tiled scan of the bins -- a
-    second pass when there is more than one tile of 8192 -- and scatter)."""
+    second pass when there is more than one tile of 8192 -- scatter of the
+    rays, and the gather that puts the hits back in order)."""
     g = opts.get("sort_cell_log2", 0) if opts else 0
     if not g:
         return 1
     nbins = 8 << sum(min(max(ld - g, 0), 5) for ld in log2_dim)
-    return 1 + 3 + (1 if nbins > 8192 else 0)
+    return 1 + 4 + (1 if nbins > 8192 else 0)
 
 
 def pcie_both_ways_gbs(nbytes: int = 256 << 20, reps: int = 5) -> float:

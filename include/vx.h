@@ -237,9 +237,12 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
  *   sort_cell_log2  0 = trace rays in the given order; g in [1, 15] = first
  *          sort them by (direction octant, Morton code of the origin's cell of
  *          side 2^g) for coherence; hits still land in the caller's order.
- *          Sorting takes 12 B per ray plus at most 1 MiB + 384 B of device
- *          scratch from CUDA's stream-ordered allocator (cudaMallocAsync), at
- *          most 2^32 - 1 rays per call;
+ *          The sort copies the rays into key order, the trace writes hits
+ *          in that order and a gather puts each back at its ray's index, so
+ *          the trace reads and writes whole sectors in order.  Sorting takes
+ *          40 B per ray plus one hit record per ray, plus at most 1 MiB +
+ *          384 B, of device scratch from CUDA's stream-ordered allocator
+ *          (cudaMallocAsync), at most 2^32 - 1 rays per call;
  *   restart 0 = octree levels keep a per-ray stack of the nodes entered;
  *          1 = restarting sparse-voxel intersection (Sec. 4.4): keep only
  *          each format level's root and walk an SVO / SVDAG level again from

@@ -204,19 +204,25 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
     const int stack = restart ? -1 : (o ? o->short_stack : 0);
     cudaStream_t st = (cudaStream_t)stream;
     // Optional coherence sort: scratch from the stream-ordered pool, freed
-    // on the same stream after the trace.
+    // on the same stream after the trace.  The trace then runs on the sorted
+    // copy of the rays into sorted hits, which a gather puts back in order.
     void* scratch = nullptr;
-    uint32_t* order = nullptr;
+    SortedRays sorted;
+    const vx_ray* trays = rays;
+    void* thits = hits;
     if (sort > 0) {
-        const uint64_t bytes = sort_scratch_bytes(v.spec.ldim, sort, n, nullptr);
+        const uint32_t hb = layout == VX_HIT_FULL ? 16u : 8u;
+        const uint64_t bytes = sort_scratch_bytes(v.spec.ldim, sort, n, hb, nullptr);
         cudaError_t ce = cudaMallocAsync(&scratch, bytes, st);
         if (ce) return fail(ce == cudaErrorMemoryAllocation ? VX_ENOMEM : VX_ECUDA, "sort scratch: %s",
                             cudaGetErrorString(ce));
-        int rc = sort_rays(v.spec.ldim, sort, rays, n, scratch, &order, st);
+        int rc = sort_rays(v.spec.ldim, sort, rays, n, hb, scratch, &sorted, st);
         if (rc) {
             cudaFreeAsync(scratch, st);
             return rc;
         }
+        trays = sorted.rays;
+        thits = sorted.hits;
     }
     int e;
     if (mode == VX_MODE_PERSISTENT) {
@@ -230,11 +236,18 @@ int launch_trace(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, in
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
         const int bps = o ? o->blocks_per_sm : 0;
         const uint32_t stage = stage_words(v, o ? o->smem_top : 0);
-        e = v.kernels->trace_persistent(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits,
+        e = v.kernels->trace_persistent(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(trays), n, thits,
                                         layout, block, bps, refill, burst, stack, stage, st, next);
     } else {
-        e = v.kernels->trace(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(rays), order, n, hits, layout,
+        e = v.kernels->trace(v.spec.fmt, img_of(v), reinterpret_cast<const float4*>(trays), n, thits, layout,
                              block, stack, st);
+    }
+    if (!e && scratch) {
+        const int rc = unsort_hits(sorted, n, hits, layout, st);
+        if (rc) {
+            cudaFreeAsync(scratch, st);
+            return rc;
+        }
     }
     if (scratch) cudaFreeAsync(scratch, st);
     if (e) return fail(VX_ECUDA, "trace launch failed: %s", cudaGetErrorString((cudaError_t)e));

@@ -7,9 +7,12 @@
 // ones, i.e. cells of side 2^(log2 dim - 5) on that axis.  Rays with equal keys start close together and head the
 // same way, so a warp that traces consecutive sorted rays reads the same
 // nodes and takes similar paths.  A counting sort by key (histogram,
-// exclusive scan, scatter) yields `order`, the ray indices in key order; the
-// trace kernels read rays and write hits through it, so results stay in the
-// caller's order.
+// exclusive scan, scatter) gives each ray its position in key order; the
+// scatter also copies the rays there (coalesced reads, whole 32-byte sectors
+// written), the trace runs on that sorted copy writing sorted hits in order,
+// and a gather puts each hit back at its ray's index (random reads of the
+// sorted hits, which the L2 still holds, and coalesced writes).  So neither
+// the trace's ray reads nor its hit writes touch scattered partial sectors.
 #include <cuda_runtime.h>
 
 #include "trace.cuh"
@@ -127,20 +130,40 @@ __global__ void __launch_bounds__(1024) k_sort_scan_add(uint32_t* __restrict__ h
         if (base + k < nbins) hist[base + k] += off;
 }
 
+// Ray i goes to position pos = offset(key) + rank: its copy is written
+// there, and pos replaces its rank (the gather of the hits reads it).
 __global__ void __launch_bounds__(256) k_sort_scatter(const uint32_t* __restrict__ keys,
-                                                      const uint32_t* __restrict__ ranks, uint64_t n,
+                                                      uint32_t* __restrict__ ranks, uint64_t n,
                                                       const uint32_t* __restrict__ offsets,
-                                                      uint32_t* __restrict__ order) {
+                                                      const float4* __restrict__ rays,
+                                                      float4* __restrict__ sorted) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t pos = __ldg(offsets + keys[i]) + ranks[i];
-    if (pos < n) order[pos] = (uint32_t)i;  // always true when the offsets are right
+    ranks[i] = pos;
+    if (pos < n) {  // always true when the offsets are right
+        const float4 a = __ldcs(rays + 2 * i), b = __ldcs(rays + 2 * i + 1);
+        sorted[2 * (uint64_t)pos] = a;
+        sorted[2 * (uint64_t)pos + 1] = b;
+    }
+}
+
+// Hit i of the caller's order = sorted hit pos[i].
+template <class T>
+__global__ void __launch_bounds__(256) k_unsort_hits(const T* __restrict__ sorted, const uint32_t* __restrict__ pos,
+                                                     uint64_t n, T* __restrict__ hits) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t p = __ldg(pos + i);
+    if (p < n) __stcs(hits + i, __ldg(sorted + p));
 }
 
 }  // namespace
 
-// Bytes of device scratch sort_rays needs for n rays.
-uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbins_out) {
+// Device scratch of a sorted trace of n rays: the sorted rays (32 B each)
+// and hits (hit_bytes each), then keys and ranks/positions (4 B each), the
+// bins and the scan's tile totals.
+uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t hit_bytes, uint32_t* nbins_out) {
     int mbits = 0;
     for (int i = 0; i < 3; i++) {
         int b = ldim[i] - g;
@@ -150,12 +173,13 @@ uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbin
     }
     const uint32_t nbins = 8u << mbits;
     if (nbins_out) *nbins_out = nbins;
-    return 3 * n * sizeof(uint32_t) + ((uint64_t)nbins + kScanMaxTiles) * sizeof(uint32_t) + 256;
+    return n * (32ull + hit_bytes + 8ull) + ((uint64_t)nbins + kScanMaxTiles) * sizeof(uint32_t) + 256;
 }
 
-// Fills order[0..n) (inside `scratch`) with ray indices sorted by key.
-int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* scratch, uint32_t** order_out,
-              cudaStream_t st) {
+// Sorts the rays into scratch: *sorted_rays receives the rays in key order,
+// *sorted_hits the space for their hits, *pos each ray's position in it.
+int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, uint32_t hit_bytes, void* scratch,
+              SortedRays* out, cudaStream_t st) {
     if (n >= 0xFFFFFFFFull) return fail(VX_EINVAL, "sorted tracing supports fewer than 2^32 rays per call");
     KeyParams kp;
     kp.g = g;
@@ -170,22 +194,42 @@ int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* sc
         kp.mbits += b;
     }
     const uint32_t nbins = 8u << kp.mbits;
-    uint32_t* keys = static_cast<uint32_t*>(scratch);
+    char* base = static_cast<char*>(scratch);
+    float4* sorted = reinterpret_cast<float4*>(base);
+    void* shits = base + 32 * n;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(base + (32ull + hit_bytes) * n);
     uint32_t* ranks = keys + n;
-    uint32_t* order = ranks + n;
-    uint32_t* hist = order + n;
+    uint32_t* hist = ranks + n;
     uint32_t* tile_sums = hist + nbins;
     const uint32_t tiles = (nbins + kScanTile - 1) / kScanTile;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nbins * sizeof(uint32_t), st);
     if (e) return fail(VX_ECUDA, "sort memset: %s", cudaGetErrorString(e));
     const unsigned grid = (unsigned)((n + 255) / 256);
-    k_sort_hist<<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(rays), n, kp, keys, ranks, hist);
+    const float4* r4 = reinterpret_cast<const float4*>(rays);
+    k_sort_hist<<<grid, 256, 0, st>>>(r4, n, kp, keys, ranks, hist);
     k_sort_scan_tiles<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
     if (tiles > 1) k_sort_scan_add<<<tiles, 1024, 0, st>>>(hist, nbins, tile_sums);
-    k_sort_scatter<<<grid, 256, 0, st>>>(keys, ranks, n, hist, order);
+    k_sort_scatter<<<grid, 256, 0, st>>>(keys, ranks, n, hist, r4, sorted);
     e = cudaGetLastError();
     if (e) return fail(VX_ECUDA, "sort launch: %s", cudaGetErrorString(e));
-    *order_out = order;
+    out->rays = reinterpret_cast<const vx_ray*>(sorted);
+    out->hits = shits;
+    out->pos = ranks;
+    return VX_OK;
+}
+
+// Puts the hits of a sorted trace back in the caller's order.
+int unsort_hits(const SortedRays& s, uint64_t n, void* hits, int layout, cudaStream_t st) {
+    if (n == 0) return VX_OK;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (layout == VX_HIT_FULL)
+        k_unsort_hits<uint4><<<grid, 256, 0, st>>>(static_cast<const uint4*>(s.hits), s.pos, n,
+                                                   static_cast<uint4*>(hits));
+    else
+        k_unsort_hits<uint2><<<grid, 256, 0, st>>>(static_cast<const uint2*>(s.hits), s.pos, n,
+                                                   static_cast<uint2*>(hits));
+    cudaError_t e = cudaGetLastError();
+    if (e) return fail(VX_ECUDA, "unsort launch: %s", cudaGetErrorString(e));
     return VX_OK;
 }
 

@@ -909,15 +909,13 @@ __device__ __forceinline__ RayIn pinhole_ray(const CamDev& c, uint32_t px, uint3
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-// `order` (optional): launch slot k traces ray order[k] and writes its hit
-// at order[k] (rays sorted for coherence, results in the caller's order).
+// Ray k of the launch writes hit k (a sorted trace runs on the sorted copies
+// of the rays and hits, sort.cu).
 template <class F, int LAYOUT, int SM = 0>
-__global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __restrict__ rays,
-                                               const uint32_t* __restrict__ order, uint64_t n,
+__global__ void VX_PLAIN_BOUNDS k_trace(F f, const Img pool, const float4* __restrict__ rays, uint64_t n,
                                                void* __restrict__ hits, uint32_t sdm) {
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const uint64_t i = order ? (uint64_t)__ldg(order + k) : k;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
     const RayIn r = load_ray(rays, i);
     Cnt cnt;
     const HitRec h = trace_ray<false, F, SM>(f, pool, r, cnt, nullptr, sdm);
@@ -1016,8 +1014,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
 // 4 top_words bytes of dynamic shared memory.
 template <class F, int LAYOUT, int SM = 0, bool TS = false>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, const Img pool,
-                                                          const float4* __restrict__ rays,
-                                                          const uint32_t* __restrict__ order, uint64_t n,
+                                                          const float4* __restrict__ rays, uint64_t n,
                                                           void* __restrict__ hits, unsigned long long* next,
                                                           int refill, int burst, uint32_t top_words,
                                                           uint32_t sdm) {
@@ -1048,7 +1045,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_persistent(F f, 
             if (!live) {
                 const uint64_t slot = base + __popc(idle & lt_mask);
                 if (slot < n) {
-                    idx = order ? (uint64_t)__ldg(order + slot) : slot;
+                    idx = slot;
                     HitRec h;
                     if (w.start(f, pool, load_ray(rays, idx), h)) store_hit<LAYOUT>(f, hits, idx, h);
                     else live = true;
@@ -1172,14 +1169,14 @@ struct KernelSet {
     bool specialized;
     FmtParams params;
     // stack: 0 full node stack, -1 restarting traversal (Sec. 4.4), D in {1, 2, 4, 8}: short stack of depth D
-    int (*trace)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+    int (*trace)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n,
                  void* hits, int layout, int block, int stack, cudaStream_t st);
     int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
                   int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                        int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
                        uint32_t* sectors);
-    int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
+    int (*trace_persistent)(const FmtParams& p, const Img pool, const float4* rays,
                             uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill, int burst,
                             int stack, uint32_t stage_words, cudaStream_t st, unsigned long long* next);
     // grid = 0: as many blocks as fit on the GPU; returns the launched grid in *grid_out.
@@ -1195,23 +1192,23 @@ template <class F>
 struct Launch {
     static F make(const FmtParams& p);
     template <int SM>
-    static int trace_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+    static int trace_as(const FmtParams& p, const Img pool, const float4* rays, uint64_t n,
                         void* hits, int layout, int block, uint32_t depth, cudaStream_t st) {
         const F f = make(p);
         const uint64_t grid = (n + (uint64_t)block - 1) / (uint64_t)block;
         const size_t sm = stack_bytes(p.J, block, depth);
         const uint32_t sdm = depth ? depth - 1u : 0u;
         prefer_carveout(layout == 0 ? (const void*)k_trace<F, 0, SM> : (const void*)k_trace<F, 1, SM>, sm, block);
-        if (layout == 0) k_trace<F, 0, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits, sdm);
-        else k_trace<F, 1, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, order, n, hits, sdm);
+        if (layout == 0) k_trace<F, 0, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, sdm);
+        else k_trace<F, 1, SM><<<(unsigned)grid, block, sm, st>>>(f, pool, rays, n, hits, sdm);
         return (int)cudaGetLastError();
     }
-    static int trace(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order, uint64_t n,
+    static int trace(const FmtParams& p, const Img pool, const float4* rays, uint64_t n,
                      void* hits, int layout, int block, int stack, cudaStream_t st) {
         if (n == 0) return 0;
-        if (stack < 0) return trace_as<1>(p, pool, rays, order, n, hits, layout, block, 0, st);
-        if (stack > 0) return trace_as<2>(p, pool, rays, order, n, hits, layout, block, (uint32_t)stack, st);
-        return trace_as<0>(p, pool, rays, order, n, hits, layout, block, 0, st);
+        if (stack < 0) return trace_as<1>(p, pool, rays, n, hits, layout, block, 0, st);
+        if (stack > 0) return trace_as<2>(p, pool, rays, n, hits, layout, block, (uint32_t)stack, st);
+        return trace_as<0>(p, pool, rays, n, hits, layout, block, 0, st);
     }
     static int trace_count(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                            int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
@@ -1231,7 +1228,7 @@ struct Launch {
         return (int)cudaGetLastError();
     }
     template <int SM, bool TS>
-    static int persistent_as(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
+    static int persistent_as(const FmtParams& p, const Img pool, const float4* rays,
                              uint64_t n, void* hits, int layout, int block, int per_sm_req, int refill, int burst,
                              cudaStream_t st, unsigned long long* next, uint32_t tw, uint32_t depth = 0) {
         const F f = make(p);
@@ -1266,10 +1263,10 @@ struct Launch {
         if (e) return (int)e;
         const unsigned g = (unsigned)grid;
         if (layout == 0)
-            k_trace_persistent<F, 0, SM, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw,
+            k_trace_persistent<F, 0, SM, TS><<<g, block, smem, st>>>(f, pool, rays, n, hits, next, refill, burst, tw,
                                                                     sdm);
         else
-            k_trace_persistent<F, 1, SM, TS><<<g, block, smem, st>>>(f, pool, rays, order, n, hits, next, refill, burst, tw,
+            k_trace_persistent<F, 1, SM, TS><<<g, block, smem, st>>>(f, pool, rays, n, hits, next, refill, burst, tw,
                                                                     sdm);
         return (int)cudaGetLastError();
     }
@@ -1277,22 +1274,22 @@ struct Launch {
     // stage_words: stage the image's first stage_words words (at most
     // kTopSmemMaxWords; the top node levels of a relocated image) in shared
     // memory, 0 = none (not combined with restart or a short stack).
-    static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays, const uint32_t* order,
+    static int trace_persistent(const FmtParams& p, const Img pool, const float4* rays,
                                 uint64_t n, void* hits, int layout, int block, int blocks_per_sm, int refill,
                                 int burst, int stack, uint32_t stage_words, cudaStream_t st,
                                 unsigned long long* next) {
         if (n == 0) return 0;
         const uint32_t tw = stage_words <= kTopSmemMaxWords ? stage_words : 0u;
         if (stack < 0)
-            return persistent_as<1, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+            return persistent_as<1, false>(p, pool, rays, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0);
         if (stack > 0)
-            return persistent_as<2, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+            return persistent_as<2, false>(p, pool, rays, n, hits, layout, block, blocks_per_sm, refill,
                                            burst, st, next, 0, (uint32_t)stack);
         if (tw)
-            return persistent_as<0, true>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+            return persistent_as<0, true>(p, pool, rays, n, hits, layout, block, blocks_per_sm, refill,
                                           burst, st, next, tw);
-        return persistent_as<0, false>(p, pool, rays, order, n, hits, layout, block, blocks_per_sm, refill,
+        return persistent_as<0, false>(p, pool, rays, n, hits, layout, block, blocks_per_sm, refill,
                                        burst, st, next, 0);
     }
     static int resident_blocks(const FmtParams& p, int layout, int block, int* per_sm) {

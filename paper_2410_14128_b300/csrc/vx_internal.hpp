@@ -191,9 +191,17 @@ struct BatchItemIn {
 // kernel (2k before, 2k + 1 after) on its stream; *groups receives the count.
 int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream,
                  void** events = nullptr, uint32_t n_events = 0, uint32_t* groups = nullptr);
-uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t* nbins_out);
-int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, void* scratch, uint32_t** order_out,
-              struct CUstream_st* st);
+// Coherence sort (sort.cu): rays copied in key order into scratch, space for
+// their hits in that order, and each ray's position.
+struct SortedRays {
+    const vx_ray* rays = nullptr;
+    void* hits = nullptr;
+    const uint32_t* pos = nullptr;
+};
+uint64_t sort_scratch_bytes(const int ldim[3], int g, uint64_t n, uint32_t hit_bytes, uint32_t* nbins_out);
+int sort_rays(const int ldim[3], int g, const vx_ray* rays, uint64_t n, uint32_t hit_bytes, void* scratch,
+              SortedRays* out, struct CUstream_st* st);
+int unsort_hits(const SortedRays& s, uint64_t n, void* hits, int layout, struct CUstream_st* st);
 int trace_noalloc(const Volume& v, const vx_ray* rays, uint64_t n, void* hits, int layout, void* stream);
 int camera_params(const vx_camera* cam, CameraParams* out);
 

@@ -50,13 +50,14 @@ def test_two_rank_throughput_gloo():
 
 def test_launch_count_includes_the_sort():
     # gpu_launches counts the sort's kernels when the options sort: histogram,
-    # scan of 8192-bin tiles (plus a second pass past one tile), scatter
+    # scan of 8192-bin tiles (plus a second pass past one tile), scatter, and the
+    # gather of the hits
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     d = (9, 9, 9)
     assert bench.trace_launches(None, d) == 1
     assert bench.trace_launches({"sort_cell_log2": 0}, d) == 1
-    assert bench.trace_launches({"sort_cell_log2": 6}, d) == 4   # 8 x 8^3 = 4096 bins: one tile
-    assert bench.trace_launches({"sort_cell_log2": 4}, d) == 5   # 8 x 32^3 bins: several tiles
-    assert bench.trace_launches({"sort_cell_log2": 9}, d) == 4   # one cell: 8 bins
+    assert bench.trace_launches({"sort_cell_log2": 6}, d) == 5   # 8 x 8^3 = 4096 bins: one tile
+    assert bench.trace_launches({"sort_cell_log2": 4}, d) == 6   # 8 x 32^3 bins: several tiles
+    assert bench.trace_launches({"sort_cell_log2": 9}, d) == 5   # one cell: 8 bins
