@@ -411,13 +411,22 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (e) break;
     }
     int rc = e ? fail(VX_ECUDA, "batch fork: %s", cudaGetErrorString(e)) : VX_OK;
+    // Timing events: inside a stream capture a record needs
+    // cudaEventRecordExternal to become an event node of the graph (a plain
+    // record there is only a dependency edge); outside a capture that flag is
+    // not allowed.
+    unsigned int rec_flags = cudaEventRecordDefault;
+    if (events && !rc) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(st, &cs);
+        if (e) rc = fail(VX_ECUDA, "batch capture state: %s", cudaGetErrorString(e));
+        else if (cs == cudaStreamCaptureStatusActive) rec_flags = cudaEventRecordExternal;
+    }
     for (int i = 0; i < nsub && !rc; i++) {
         Sub& g = subs[i];
         cudaStream_t fs = F.s[i % kForkStreams];
         const bool timed = events && (uint32_t)(2 * i + 1) < n_events;
-        // cudaEventRecordExternal: inside a stream capture the record becomes
-        // an event node of the graph (a plain record there is only an edge)
-        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i], fs, cudaEventRecordExternal))) {
+        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i], fs, rec_flags))) {
             rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
             break;
         }
@@ -427,7 +436,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
             rc = fail(VX_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)lr));
             break;
         }
-        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i + 1], fs, cudaEventRecordExternal))) {
+        if (timed && (e = cudaEventRecordWithFlags((cudaEvent_t)events[2 * i + 1], fs, rec_flags))) {
             rc = fail(VX_ECUDA, "batch timing event: %s", cudaGetErrorString(e));
             break;
         }

@@ -403,6 +403,36 @@ def test_batch_in_cuda_graph():
                 assert np.array_equal(vx.hits_to_numpy(h), gpu_trace(vols[v], r_np, mode=vx.MODE_PLAIN)), rep
 
 
+def test_batch_timed_records_each_group_kernel():
+    # vx_trace_batch_timed: the same hits, and one (start, end) pair of events
+    # per group with a positive interval, called directly and inside a graph
+    vols, grids, sets = _batch_setup(203, 24)
+    dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
+    items = [(vols[v], r, h) for v, r, h in dev]
+    vx.trace_batch(items)
+    torch.cuda.synchronize()
+    ref = [h.clone() for _, _, h in dev]
+    groups = len({v for v, r in sets if len(r)})
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(2 * groups)]
+    for e in events:
+        e.record()
+    for _, _, h in dev:
+        h.fill_(-1)
+    assert vx.trace_batch(items, events=events) == groups
+    torch.cuda.synchronize()
+    assert all(torch.equal(h, r) for (_, _, h), r in zip(dev, ref))
+    assert all(events[2 * k].elapsed_time(events[2 * k + 1]) > 0 for k in range(groups))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        vx.trace_batch(items, events=events)
+    for _, _, h in dev:
+        h.fill_(-1)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(h, r) for (_, _, h), r in zip(dev, ref))
+    assert all(events[2 * k].elapsed_time(events[2 * k + 1]) > 0 for k in range(groups))
+
+
 @pytest.mark.parametrize("spec", ["R(3,3,3) S(2) G(2)", "G(7)", "R(2,2,2) G(2) G(3)", "S(2) G(2) R(3,3,3)"])
 def test_packed_device_image_equals_canonical(spec):
     g = synth.terrain_volume(87, 128)
