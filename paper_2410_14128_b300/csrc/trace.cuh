@@ -336,12 +336,12 @@ constexpr uint32_t kTopSmemMaxWords = 8192;  // 32 KiB of staged image words at 
 // (launch.cu).
 void prefer_carveout(const void* kernel, size_t smem_per_block, int block);
 
-// Entries per thread: one {pointer, valid mask} per node level, then three
+// Entries per thread: one {pointer, valid mask} per node level, then two
 // holding values a walk reads rarely -- {start voxel x, y}, {start voxel z,
-// tmax}, {position guard band, unused} -- which would otherwise take
-// registers; the stride rounds that up to an odd count.  A short stack
-// (mode 2) adds its ring of D entries after those.
-__host__ __device__ constexpr uint32_t stack_entries(uint32_t J, uint32_t D = 0) { return J + 3u + D; }
+// tmax} -- which would otherwise take registers; the stride rounds that up to
+// an odd count.  A short stack (mode 2) adds its ring of D entries after
+// those.
+__host__ __device__ constexpr uint32_t stack_entries(uint32_t J, uint32_t D = 0) { return J + 2u + D; }
 __host__ __device__ constexpr uint32_t stack_stride(uint32_t J, uint32_t D = 0) { return stack_entries(J, D) | 1u; }
 inline size_t stack_bytes(uint32_t J, int block, uint32_t D = 0) {
     return (size_t)stack_stride(J, D) * (size_t)block * sizeof(uint2);
@@ -356,6 +356,7 @@ struct Walker {
     float gabs;  // guard band: 2^-20 of the largest |t| this walk compares
     // (direction sign per axis, -1 / 0 / 1: sgn(), from the ray)
     int c[3];  // cell at node level j (the start voxel is kept in the stack array)
+    float gpos;  // guard band for positions o + t d inside the grid (read by descents)
     int j, la, budget;
     int skip;  // DF level: cells the walk may still enter without a look-up
     bool fresh;
@@ -400,7 +401,7 @@ struct Walker {
 
 
     // Node-stack entry e of this thread (0 <= e < stack_entries(J); entries
-    // J .. J + 2 hold the start voxel, tmax and the position guard band).  Every index the walk forms lies in
+    // J and J + 1 hold the start voxel and tmax).  Every index the walk forms lies in
     // that range by construction (j only grows by descents below J - 1 and
     // pops to jpop(h) <= j); the instrumented walker also checks it and
     // refuses an access outside it (counted like a refused read).
@@ -598,10 +599,8 @@ struct Walker {
         gabs = kGuard * fmaxf(fabsf(te), fabsf(tx));
         // o + t d (FP32) is off by at most |d| 3 2^-24 |t| + 2^-24 |p|, with
         // |t| <= max(|te|, |tx|) and |p| within the grid where it matters.
-        // (read by descents only: kept in the thread's shared-memory entries)
-        const float gpos = gabs * fmaxf(fabsf(r.d[0]), fmaxf(fabsf(r.d[1]), fabsf(r.d[2]))) +
-                           kGuard * (float)(2 << max(f.ldim(0), max(f.ldim(1), f.ldim(2))));
-        sput(f, f.J() + 2, make_uint2(__float_as_uint(gpos), 0u));
+        gpos = gabs * fmaxf(fabsf(r.d[0]), fmaxf(fabsf(r.d[1]), fabsf(r.d[2]))) +
+               kGuard * (float)(2 << max(f.ldim(0), max(f.ldim(1), f.ldim(2))));
         // A ray crosses at most nx + ny + nz cells of any level and each step
         // costs at most J descents; past this bound the ray reports ST_ERROR.
         budget = ((1 << f.ldim(0)) + (1 << f.ldim(1)) + (1 << f.ldim(2)) + 4) * (f.J() + 2);
@@ -678,7 +677,7 @@ struct Walker {
             if (SMODE == 1) {
                 restart(f, im);
             } else if (SMODE == 2 && !((f.top() >> j) & 1u)) {
-                const uint2 e = sget(f, f.J() + 3 + (j & (int)sdm));
+                const uint2 e = sget(f, f.J() + 2 + (j & (int)sdm));
                 if ((e.y >> 8) == (uint32_t)(j + 1)) {
                     Pc = e.x;
                     Mc = e.y & 0xFFu;
@@ -780,7 +779,7 @@ struct Walker {
             }
             ++j;
             if (SMODE == 0 || ((f.top() >> j) & 1u)) sput(f, j, make_uint2(Pn, Mn));
-            else if (SMODE == 2) sput(f, J + 3 + (j & (int)sdm), make_uint2(Pn, Mn | ((uint32_t)(j + 1) << 8)));
+            else if (SMODE == 2) sput(f, J + 2 + (j & (int)sdm), make_uint2(Pn, Mn | ((uint32_t)(j + 1) << 8)));
             Pc = Pn;
             Mc = Mn;
             const int sn = ls(f), bn = lb(f, 0);
@@ -803,7 +802,7 @@ struct Walker {
                 int cn = (int)fminf(fmaxf(floorf(q), (float)base), (float)topc);
                 const float rq = rintf(q);
                 if (rq > (float)base && rq <= (float)topc &&
-                    fabsf(q - rq) <= __uint_as_float(sget(f, J + 2).x) * scale) {
+                    fabsf(q - rq) <= gpos * scale) {
                     VX_CNT(fp64, 1);
                     const int B = (int)rq;
                     // plane of the crossing that entered the parent's cell (voxel units):
