@@ -221,8 +221,9 @@ int vx_decode_brick(vx_volume v, uint32_t x0, uint32_t y0, uint32_t z0, uint32_t
 
 /* Trace options (NULL = defaults / autotuned values).
  *   mode   VX_MODE_*;
- *   block  threads per block: 0 = default (256; 128 for the plain render
- *          kernel), else a multiple of 32 in [32, 256] (VX_EINVAL otherwise);
+ *   block  threads per block: 0 = default (256 for persistent kernels, 64
+ *          for the plain trace kernel, 128 for the plain render kernel),
+ *          else a multiple of 32 in [32, 256] (VX_EINVAL otherwise);
  *   blocks_per_sm  persistent mode: resident blocks per SM, 0 = as many as fit;
  *   smem_top  persistent mode, staging depth: k in [1, 8] = each block first
  *          copies the structures of the top k node levels (any level kind:
@@ -371,6 +372,24 @@ int vx_trace_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layou
  * plus VX_EINVAL for n_events > 0 with events NULL. */
 int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
                          void* stream, void** events, uint32_t n_events, uint32_t* groups);
+
+/* vx_trace_batch for rays and hits in host memory (items[k].rays and
+ * .hits are host pointers, aligned as for vx_trace_batch; page-locked memory
+ * gives full-speed asynchronous copies, pageable memory works but its copies
+ * do not overlap).  The rays of all items stream through the device in waves
+ * of at most 2^22 rays, taken in item order (an item larger than the room
+ * left in a wave is split across waves); each wave is uploaded, traced by
+ * the batched kernels (as vx_trace_batch: one persistent kernel per format,
+ * each volume's tuned options unless opts is given) and its hits copied
+ * back, with three waves in flight on three internal streams, so uploads,
+ * kernels and downloads overlap.  The first wave starts after the caller's
+ * earlier work on `stream`; the call returns when every hit is in host
+ * memory.  Device scratch: three wave buffers of 192 MiB, allocated on the
+ * first call per device and kept for the process; calls on one device run
+ * one at a time.  Errors as vx_trace_batch; on an error the call still
+ * waits for the copies it issued before returning. */
+int vx_trace_batch_host(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
+                        void* stream);
 
 /* Picks vx_trace options for this volume: times candidates on `rays` (a
  * device sample of the rays the caller will trace, n of them) with CUDA

@@ -104,6 +104,8 @@ _SIGS = {
                                             ctypes.POINTER(_TraceOpts), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
                                             ctypes.POINTER(ctypes.c_uint32)]),
+    "vx_trace_batch_host": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
+                                           ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                    ctypes.POINTER(_TraceOpts), ctypes.POINTER(ctypes.c_double)]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -449,6 +451,26 @@ def trace_batch(items, layout: int = HIT_FULL, stream=None, events=None, **opts)
     _check(lib().vx_trace_batch_timed(arr, len(items), layout, op, _stream_handle(stream), ev, len(events),
                                       ctypes.byref(groups)))
     return groups.value
+
+
+def trace_batch_host(items, layout: int = HIT_FULL, stream=None, **opts) -> None:
+    """items: list of (Volume, rays, hits) with rays a C-contiguous float32
+    (n, 8) numpy array and hits a numpy array of n hit records (hit_dtype),
+    both in host memory (page-locked for overlapped copies); one
+    vx_trace_batch_host call, which returns when the hits are written."""
+    arr = (_BatchItem * max(1, len(items)))()
+    for k, (vol, rays, hits) in enumerate(items):
+        if not (rays.flags["C_CONTIGUOUS"] and rays.dtype == np.float32 and rays.ndim == 2 and rays.shape[1] == 8):
+            raise ValueError("rays must be a C-contiguous float32 (n, 8) array")
+        if not hits.flags["C_CONTIGUOUS"] or hits.nbytes != rays.shape[0] * hit_dtype(layout).itemsize:
+            raise ValueError("hits must be a C-contiguous array of n hit records for the layout")
+        arr[k].volume = vol.handle
+        arr[k].rays = rays.ctypes.data
+        arr[k].n = rays.shape[0]
+        arr[k].hits = hits.ctypes.data
+    o = _opts(**opts) if opts else None
+    op = ctypes.byref(o) if o is not None else None
+    _check(lib().vx_trace_batch_host(arr, len(items), layout, op, _stream_handle(stream)))
 
 
 def raygen_ao(rays, hits, seed: int, spp: int = 8, eps: float = 1e-3, tmax: float = 32.0, out=None, stream=None):

@@ -416,6 +416,35 @@ extern "C" int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, 
     return launch_batch(in, hit_layout, opts, stream, events, n_events, groups);
 }
 
+extern "C" int vx_trace_batch_host(const vx_batch_item* items, uint32_t count, int32_t hit_layout,
+                                   const vx_trace_opts* opts, void* stream) {
+    clear_error();
+    if (count == 0) return VX_OK;
+    if (!items) return fail(VX_EINVAL, "items is NULL");
+    if (count > 65536) return fail(VX_EINVAL, "at most 65536 items per batch");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (opts && opts->sort_cell_log2 != 0) return fail(VX_EUNSUPPORTED, "batched tracing does not sort rays");
+    int dev = -1;
+    std::vector<BatchItemIn> in;
+    in.reserve(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const vx_batch_item& it = items[i];
+        rc = check_trace_args(it.volume, it.rays, it.n, it.hits, hit_layout);
+        if (rc) return fail(rc, "item %u: %s", i, vx_last_error());
+        if (it.n == 0) continue;
+        if ((rc = check_ptrs(it.rays, it.hits, hit_layout))) return fail(rc, "item %u: %s", i, vx_last_error());
+        if (!it.rays) return fail(VX_EINVAL, "item %u: rays is NULL", i);
+        if (dev < 0) dev = it.volume->v.device;
+        else if (it.volume->v.device != dev) return fail(VX_EINVAL, "item %u: all volumes must be on one device", i);
+        in.push_back(BatchItemIn{&it.volume->v, it.rays, it.n, it.hits});
+    }
+    if (in.empty()) return VX_OK;
+    DeviceScope ds(dev);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return launch_batch_host(in, hit_layout, opts, stream);
+}
+
 // ---------------------------------------------------------------------------
 // Autotuner: coordinate descent over the trace options, each candidate timed
 // with CUDA events on the sample (best of 3 runs after one warm-up run).

@@ -952,18 +952,25 @@ __global__ void VX_PLAIN_BOUNDS k_trace_count(F f, const Img pool,
     }
 }
 
+constexpr uint32_t kTileW = 8, kTileH = 32 / kTileW;  // pixels of a warp's tile
+
 // Persistent render: like k_trace_persistent, with the rays generated from
-// the queue slots (pixel i0 + slot) instead of read from memory.
+// the queue slots instead of read from memory.  Slot s is lane s % 32 of tile
+// s / 32, the tiles of 8 x 4 pixels taken row by row over the image rows from
+// y0 (the order of the plain render kernel's warps), so the lanes one refill
+// hands out sit in one or two neighbouring tiles.  Slots of pixels outside
+// the image or outside [i0, i0 + n) are taken and dropped.
 template <class F, int LAYOUT>
 __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f, const Img pool, CamDev cam, uint64_t i0,
-                                                           uint64_t n, void* __restrict__ hits,
+                                                           uint64_t n, uint32_t y0, uint32_t tiles_w, uint64_t slots,
+                                                           void* __restrict__ hits,
                                                            unsigned long long* next, int refill, int burst) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     Walker<false, F> w;  // node stack in the kernel's dynamic shared memory
     bool live = false;
     bool exhausted = false;  // warp-uniform
-    uint64_t slot = 0;
+    uint64_t pix = 0;        // hit index (pixel - i0) of the lane's ray
     while (true) {
         const unsigned idle = __ballot_sync(0xffffffffu, !live);
         if (exhausted) {
@@ -973,15 +980,30 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
             unsigned long long base = 0;
             if ((int)lane == leader) base = atomicAdd(next, (unsigned long long)__popc(idle));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (base + (unsigned long long)__popc(idle) >= n) exhausted = true;
+            if (base + (unsigned long long)__popc(idle) >= slots) exhausted = true;
             if (!live) {
-                slot = base + __popc(idle & lt_mask);
-                if (slot < n) {
-                    const uint64_t i = i0 + slot;
-                    const RayIn r = pinhole_ray(cam, (uint32_t)(i % cam.W), (uint32_t)(i / cam.W));
-                    HitRec h;
-                    if (w.start(f, pool, r, h)) store_hit<LAYOUT>(f, hits, slot, h);
-                    else live = true;
+                const uint64_t slot = base + __popc(idle & lt_mask);
+                if (slot < slots) {
+                    uint32_t trow, tcol;
+                    if (slots < (1ull << 37)) {  // tile index below 2^32: 32-bit division
+                        const uint32_t tile = (uint32_t)(slot >> 5);
+                        trow = tile / tiles_w;
+                        tcol = tile - trow * tiles_w;
+                    } else {
+                        const uint64_t tile = slot >> 5;
+                        trow = (uint32_t)(tile / tiles_w);
+                        tcol = (uint32_t)(tile - (uint64_t)trow * tiles_w);
+                    }
+                    const uint32_t px = tcol * kTileW + ((uint32_t)slot % kTileW);
+                    const uint64_t py = (uint64_t)y0 + (uint64_t)trow * kTileH + (((uint32_t)slot & 31u) / kTileW);
+                    const uint64_t i = py * cam.W + px;
+                    if (px < cam.W && i >= i0 && i - i0 < n) {
+                        pix = i - i0;
+                        const RayIn r = pinhole_ray(cam, px, (uint32_t)py);
+                        HitRec h;
+                        if (w.start(f, pool, r, h)) store_hit<LAYOUT>(f, hits, pix, h);
+                        else live = true;
+                    }
                 }
             }
             continue;
@@ -990,7 +1012,7 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_render_persistent(F f,
             for (int k = 0; k < burst; k++) {
                 HitRec h;
                 if (w.step(f, pool, h)) {
-                    store_hit<LAYOUT>(f, hits, slot, h);
+                    store_hit<LAYOUT>(f, hits, pix, h);
                     live = false;
                     break;
                 }
@@ -1136,21 +1158,19 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     }
 }
 
-constexpr uint32_t kTileW = 8, kTileH = 32 / kTileW;  // pixels of a warp's tile
-
 template <class F, int LAYOUT>
 __global__ void VX_PLAIN_BOUNDS k_render(F f, const Img pool, CamDev cam, uint64_t i0,
-                                                uint64_t n, uint32_t y0, uint32_t tiles_w,
-                                                void* __restrict__ hits) {
-    // Each warp takes a tile of 8 x 4 pixels (tiles row by row from image row
-    // y0): neighbouring rays follow nearly the same path through the format,
-    // and a compact tile has fewer lanes on a silhouette than a 32-pixel run.
-    // Pixels outside the image or outside [i0, i0 + n) are skipped.
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t tile = t >> 5;
-    const uint32_t lane = (uint32_t)t & 31u;
-    const uint32_t px = (uint32_t)(tile % tiles_w) * kTileW + (lane % kTileW);
-    const uint64_t py = (uint64_t)y0 + (tile / tiles_w) * kTileH + (lane / kTileW);
+                                                uint64_t n, uint32_t y0, void* __restrict__ hits) {
+    // Each warp takes a tile of 8 x 4 pixels: neighbouring rays follow nearly
+    // the same path through the format, and a compact tile has fewer lanes on
+    // a silhouette than a 32-pixel run.  blockIdx.y is the tile row (image
+    // rows y0 + 4 blockIdx.y ...), the x threads run along it, a warp per
+    // tile, so no thread divides to find its pixel.  Pixels outside the image
+    // or outside [i0, i0 + n) are skipped.
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t px = (t >> 5) * kTileW + (lane % kTileW);
+    const uint64_t py = (uint64_t)y0 + (uint64_t)blockIdx.y * kTileH + (lane / kTileW);
     if (px >= cam.W) return;
     const uint64_t i = py * cam.W + px;
     if (i < i0 || i - i0 >= n) return;
@@ -1326,33 +1346,47 @@ struct Launch {
                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_persistent<F, 1>, block, sm);
         if (e) return (int)e;
         if (per_sm < 1) per_sm = 1;
+        // queue slots: 32 per 8 x 4 pixel tile over the rows holding pixels i0 .. i0 + n - 1
+        const uint64_t y0 = i0 / cam.W, y1 = (i0 + n - 1) / cam.W;
+        const uint64_t tiles_w = (cam.W + kTileW - 1) / kTileW, tile_rows = (y1 - y0 + kTileH) / kTileH;
+        const uint64_t slots = tiles_w * tile_rows * 32u;
         uint64_t grid = (uint64_t)sms * per_sm;
-        const uint64_t need = (n + (uint64_t)block - 1) / (uint64_t)block;
+        const uint64_t need = (slots + (uint64_t)block - 1) / (uint64_t)block;
         if (grid > need) grid = need;
         e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
         if (e) return (int)e;
         if (layout == 0)
-            k_render_persistent<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0,
+                                                                         (uint32_t)tiles_w, slots, hits, next,
+                                                                         refill, burst);
         else
-            k_render_persistent<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, hits, next, refill, burst);
+            k_render_persistent<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0,
+                                                                         (uint32_t)tiles_w, slots, hits, next,
+                                                                         refill, burst);
         return (int)cudaGetLastError();
     }
     static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
                       void* hits, int layout, int block, cudaStream_t st) {
         if (n == 0) return 0;
         const F f = make(p);
-        // 8 x 4 pixel tiles over the image rows that hold pixels i0 .. i0 + n - 1
+        // 8 x 4 pixel tiles over the image rows that hold pixels i0 .. i0 + n - 1;
+        // one grid row per tile row, at most 65535 tile rows per launch
         const uint64_t y0 = i0 / cam.W, y1 = (i0 + n - 1) / cam.W;
         const uint64_t tiles_w = (cam.W + kTileW - 1) / kTileW, tile_rows = (y1 - y0 + kTileH) / kTileH;
-        const uint64_t threads = tiles_w * tile_rows * 32u;
-        const uint64_t grid = (threads + (uint64_t)block - 1) / (uint64_t)block;
-        if (grid > 0x7FFFFFFFull) return (int)cudaErrorInvalidConfiguration;
+        const uint64_t row_threads = tiles_w * 32u;
+        if (row_threads + (uint64_t)block > 0xFFFFFFFFull) return (int)cudaErrorInvalidConfiguration;
+        const unsigned gx = (unsigned)((row_threads + (uint64_t)block - 1) / (uint64_t)block);
         const size_t sm = stack_bytes(p.J, block);
         prefer_carveout(layout == 0 ? (const void*)k_render<F, 0> : (const void*)k_render<F, 1>, sm, block);
-        if (layout == 0)
-            k_render<F, 0><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
-        else
-            k_render<F, 1><<<(unsigned)grid, block, sm, st>>>(f, pool, cam, i0, n, (uint32_t)y0, (uint32_t)tiles_w, hits);
+        constexpr uint64_t kMaxRows = 65535;
+        for (uint64_t r = 0; r < tile_rows; r += kMaxRows) {
+            const dim3 grid(gx, (unsigned)(tile_rows - r < kMaxRows ? tile_rows - r : kMaxRows));
+            const uint32_t yr = (uint32_t)(y0 + r * kTileH);
+            if (layout == 0)
+                k_render<F, 0><<<grid, block, sm, st>>>(f, pool, cam, i0, n, yr, hits);
+            else
+                k_render<F, 1><<<grid, block, sm, st>>>(f, pool, cam, i0, n, yr, hits);
+        }
         return (int)cudaGetLastError();
     }
 };

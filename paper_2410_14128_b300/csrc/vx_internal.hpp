@@ -191,6 +191,9 @@ struct BatchItemIn {
 // kernel (2k before, 2k + 1 after) on its stream; *groups receives the count.
 int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream,
                  void** events = nullptr, uint32_t n_events = 0, uint32_t* groups = nullptr);
+// The same sets with rays and hits in host memory, streamed through the device
+// in waves; returns when every hit is in host memory.
+int launch_batch_host(const std::vector<BatchItemIn>& items, int layout, const vx_trace_opts* o, void* stream);
 // Coherence sort (sort.cu): rays copied in key order into scratch, space for
 // their hits in that order, and each ray's position.
 struct SortedRays {

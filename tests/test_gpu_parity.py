@@ -228,21 +228,28 @@ def test_render_equals_trace_of_raygen():
     assert np.array_equal(hc["t"], full["t"])
 
 
-@pytest.mark.parametrize("W,H", [(7, 5), (1001, 767), (33, 4097)])
+@pytest.mark.parametrize("W,H", [(7, 5), (1001, 767), (33, 4097), (3, 300001)])
 def test_render_ragged_tiles_and_chunks(W, H):
-    # image sides that are not multiples of the 8 x 4 warp tile, and (for
-    # the host variant) chunks of 2^18 pixels that start in the middle of a row
+    # image sides that are not multiples of the 8 x 4 warp tile, an image of
+    # more than 65535 tile rows (the plain kernel splits its grid rows over
+    # launches), both render kernels (the persistent one hands out pixels in
+    # tile order), and (for the host variant) chunks of 2^18 pixels that
+    # start in the middle of a row
     g = synth.terrain_volume(43, 128)
     vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
     cam = synth.camera(44, 128, W, H, mode="above")
     rays = vx.raygen_pinhole(cam)
     h1 = vx.alloc_hits(rays.shape[0])
     vol.trace(rays, h1)
-    h2 = vx.alloc_hits(rays.shape[0])
-    vol.render(cam, h2, block=64)
-    torch.cuda.synchronize()
-    assert torch.equal(h1, h2)
+    for opts in (dict(block=64), dict(mode=vx.MODE_PLAIN, block=32), dict(mode=vx.MODE_PLAIN, block=256),
+                 dict(mode=vx.MODE_PERSISTENT), dict(mode=vx.MODE_PERSISTENT, block=64, refill=1, burst=2)):
+        h2 = vx.alloc_hits(rays.shape[0])
+        h2.fill_(-0x55555556)  # a pixel the kernel skipped keeps this pattern
+        vol.render(cam, h2, **opts)
+        torch.cuda.synchronize()
+        assert torch.equal(h1, h2), opts
     assert np.array_equal(vol.render_host(cam), vx.hits_to_numpy(h1))
+    assert np.array_equal(vol.render_host(cam, mode=vx.MODE_PERSISTENT), vx.hits_to_numpy(h1))
 
 
 def test_trace_host_multi_chunk():
@@ -380,6 +387,40 @@ def test_batch_equals_per_set_trace():
     for (v, r_np), (_, r, h) in list(zip(sets, dev))[:8]:
         if len(r_np):
             compare(grids[v], r_np, vx.hits_to_numpy(h))
+
+
+def test_batch_host_equals_device_batch():
+    # vx_trace_batch_host: sets of every size (empty ones included) and two
+    # large sets that split across the 2^22-ray waves, from page-locked and
+    # from pageable host memory, in both hit layouts: the same hits as the
+    # device-memory batch
+    vols, grids, sets = _batch_setup(204, 40)
+    sets = sets + [(0, synth.incoherent_rays(2041, 128, 3_000_000)),
+                   (2, synth.aimed_rays(2042, (64, 64, 64), 6_000_000))]
+    for layout in (vx.HIT_FULL, vx.HIT_COMPACT):
+        dt = vx.hit_dtype(layout)
+        dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r), layout)) for v, r in sets]
+        vx.trace_batch([(vols[v], r, h) for v, r, h in dev], layout=layout)
+        torch.cuda.synchronize()
+        host = []
+        for k, (v, r) in enumerate(sets):
+            rr = np.ascontiguousarray(r, dtype=np.float32)
+            if k % 3 == 0:  # pageable
+                hh = np.empty(len(r), dt)
+            else:  # page-locked
+                rr = torch.from_numpy(rr).pin_memory().numpy()
+                hh = torch.empty(len(r) * dt.itemsize, dtype=torch.uint8).pin_memory().numpy().view(dt)
+            hh.view(np.uint8)[:] = 0xAB  # a record the call skipped keeps this pattern
+            host.append((vols[v], rr, hh))
+        vx.trace_batch_host(host, layout=layout)
+        for (_, _, hh), (_, _, h) in zip(host, dev):
+            assert np.array_equal(hh.view(np.uint8), vx.hits_to_numpy(h, layout).view(np.uint8))
+    # the large sets (full records) against the oracle on a sample
+    for v, r in sets[-2:]:
+        full = np.empty(len(r), vx.HIT_DTYPE)
+        vx.trace_batch_host([(vols[v], np.ascontiguousarray(r, dtype=np.float32), full)])
+        idx = np.sort(np.random.default_rng(5).choice(len(r), 20000, replace=False))
+        compare(grids[v], r[idx], full[idx])
 
 
 def test_batch_in_cuda_graph():
