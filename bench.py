@@ -643,7 +643,7 @@ def run_headline(args):
                         "frac": round(e2e_value / world / bound, 4),
                         "peak_source": "256 MiB pinned-host copies, one up and one down at once, timed here"},
                "api": "vx_trace_batch_host: the 64 sets from pinned host memory in one call per step (waves of "
-                      "2^22 rays: upload, batched kernels and download of three waves overlapping), hits back "
+                      "2^21 rays: upload, batched kernels and download of four waves overlapping), hits back "
                       "to pinned host memory",
                "per_set_vx_trace_host_mrays_s": round(world * total * n_ps / dt_ps / 1e6, 3)}
         del host_rays, host_hits, host_items

@@ -377,14 +377,14 @@ int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit
  * .hits are host pointers, aligned as for vx_trace_batch; page-locked memory
  * gives full-speed asynchronous copies, pageable memory works but its copies
  * do not overlap).  The rays of all items stream through the device in waves
- * of at most 2^22 rays, taken in item order (an item larger than the room
+ * of at most 2^21 rays, taken in item order (an item larger than the room
  * left in a wave is split across waves); each wave is uploaded, traced by
  * the batched kernels (as vx_trace_batch: one persistent kernel per format,
  * each volume's tuned options unless opts is given) and its hits copied
- * back, with three waves in flight on three internal streams, so uploads,
+ * back, with four waves in flight on four internal streams, so uploads,
  * kernels and downloads overlap.  The first wave starts after the caller's
  * earlier work on `stream`; the call returns when every hit is in host
- * memory.  Device scratch: three wave buffers of 192 MiB, allocated on the
+ * memory.  Device scratch: four wave buffers of 96 MiB, allocated on the
  * first call per device and kept for the process; calls on one device run
  * one at a time.  Errors as vx_trace_batch; on an error the call still
  * waits for the copies it issued before returning. */

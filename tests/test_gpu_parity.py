@@ -391,7 +391,7 @@ def test_batch_equals_per_set_trace():
 
 def test_batch_host_equals_device_batch():
     # vx_trace_batch_host: sets of every size (empty ones included) and two
-    # large sets that split across the 2^22-ray waves, from page-locked and
+    # large sets that split across the 2^21-ray waves, from page-locked and
     # from pageable host memory, in both hit layouts: the same hits as the
     # device-memory batch
     vols, grids, sets = _batch_setup(204, 40)
