@@ -347,8 +347,10 @@ int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, in
  * nothing and does not synchronise, so it can be captured into a CUDA graph
  * (make one uncaptured call per device first: it creates the library's
  * fork streams).  opts: refill/burst/block as for vx_trace for every group
- * (NULL or VX_MODE_AUTO: each group's volume's tuned persistent options,
- * else the defaults); sorting is not supported
+ * (NULL or VX_MODE_AUTO: the block, refill and burst of the best
+ * persistent-kernel options vx_autotune timed for each group's volume, also
+ * when it chose the plain kernel for vx_trace; else the defaults); sorting
+ * is not supported
  * here (VX_EUNSUPPORTED).  Calls for one device are enqueued one at a time.
  * (Not in the paper: it traces one frame of one format at a time.) */
 typedef struct vx_batch_item {

@@ -554,6 +554,9 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
         for (int bu : {1, 2, 4, 8, 16, 32, 64}) { vx_trace_opts c = cur; c.burst = bu; consider(c); }
         for (int bl : {64, 128, 256}) { vx_trace_opts c = cur; c.block = bl; consider(c); }
     }
+    // the best persistent-kernel options so far: what a batched launch of
+    // this volume's sets uses when the plain kernel wins below
+    const vx_trace_opts best_persistent = cur;
     // the one-thread-per-ray kernel (sorting and restarting carry over;
     // shared-memory staging is a persistent-kernel option)
     {
@@ -573,6 +576,7 @@ extern "C" int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* st
     {
         std::lock_guard<std::mutex> lock(V.tune_mu);
         V.tuned_opts = cur;
+        V.tuned_persistent = best_persistent;
         V.tuned = true;
     }
     if (best_out) *best_out = cur;

@@ -351,9 +351,10 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         g->d.start[k + 1] = g->d.start[k] + it.n;
     }
     if (subs.empty()) return VX_OK;
-    // Options of each group: explicit ones, else its volume's tuned
-    // persistent-mode block, refill and burst (its own format's best), else
-    // the defaults (plain-mode tunings do not carry over).
+    // Options of each group: explicit ones, else the block, refill and burst
+    // of its volume's best persistent-kernel tuning (the tuned options when
+    // the autotuner chose the persistent kernel, else the best persistent
+    // candidate it timed), else the defaults.
     const int nsub = (int)subs.size();
     std::vector<vx_trace_opts> gopts(nsub);
     for (int i = 0; i < nsub; i++) {
@@ -361,7 +362,7 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (!o || o->mode == VX_MODE_AUTO) {
             Volume& mv = const_cast<Volume&>(*subs[i].v0);
             std::lock_guard<std::mutex> lock(mv.tune_mu);
-            if (mv.tuned && mv.tuned_opts.mode == VX_MODE_PERSISTENT) def = mv.tuned_opts;
+            if (mv.tuned) def = mv.tuned_opts.mode == VX_MODE_PERSISTENT ? mv.tuned_opts : mv.tuned_persistent;
         } else {
             def = *o;
         }

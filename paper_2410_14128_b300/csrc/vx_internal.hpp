@@ -149,6 +149,7 @@ struct Volume {
     std::mutex tune_mu;
     bool tuned = false;
     vx_trace_opts tuned_opts{};             // chosen by vx_autotune, used for VX_MODE_AUTO
+    vx_trace_opts tuned_persistent{};       // vx_autotune's best persistent-kernel options (batched groups)
     unsigned long long* d_queue = nullptr;  // kQueueRing + kQueueCaptured counters
     mutable std::atomic<uint32_t> queue_slot{0};
     mutable std::atomic<uint32_t> captured_slot{0};
