@@ -388,8 +388,10 @@ int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit
  * earlier work on `stream`; the call returns when every hit is in host
  * memory.  Device scratch: four wave buffers of 96 MiB, allocated on the
  * first call per device and kept for the process; calls on one device run
- * one at a time.  Errors as vx_trace_batch; on an error the call still
- * waits for the copies it issued before returning. */
+ * one at a time.  Errors as vx_trace_batch, and VX_EUNSUPPORTED when
+ * `stream` is being captured into a CUDA graph (the call waits for its
+ * copies); on an error the call still waits for the copies it issued
+ * before returning. */
 int vx_trace_batch_host(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
                         void* stream);
 
@@ -409,7 +411,9 @@ int vx_autotune(vx_volume v, const vx_ray* rays, uint64_t n, void* stream, vx_tr
 
 /* Same as vx_trace with host arrays: the rays are copied to the device in
  * chunks, traced and the hits copied back, copies overlapped with tracing.
- * Returns when all hits are in host memory.  Pinned host memory is fastest. */
+ * Returns when all hits are in host memory.  Pinned host memory is fastest.
+ * VX_EUNSUPPORTED on a stream being captured into a CUDA graph (as for
+ * vx_render_host). */
 int vx_trace_host(vx_volume v, const vx_ray* rays_host, uint64_t n, void* hits_host, int32_t hit_layout,
                   const vx_trace_opts* opts, void* stream);
 
@@ -478,7 +482,7 @@ int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t hit_layout,
               void* stream);
 
 /* Same as vx_render with the hits copied to host memory; returns when they
- * are there. */
+ * are there.  VX_EUNSUPPORTED on a stream being captured into a CUDA graph. */
 int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host, int32_t hit_layout,
                    const vx_trace_opts* opts, void* stream);
 

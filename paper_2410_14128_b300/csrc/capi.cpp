@@ -129,6 +129,12 @@ void free_staging(Staging& S) {
 // kernels of other chunks.
 template <class Work>
 int pipeline(Volume& V, uint64_t n, void* stream, Work work) {
+    // the call waits for its copies, which a stream capture cannot hold
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+    if (ce) return cuda_fail(ce, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(VX_EUNSUPPORTED, "tracing from host memory waits for its copies: not on a capturing stream");
     std::lock_guard<std::mutex> lock(V.staging_mu);
     int rc = ensure_staging(V);
     if (rc) return rc;

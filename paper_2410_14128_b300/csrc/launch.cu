@@ -519,6 +519,12 @@ int launch_batch_host(const std::vector<BatchItemIn>& items, int layout, const v
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce) return fail(VX_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
     if (dev < 0 || dev >= 64) return fail(VX_EUNSUPPORTED, "device index %d above 63", dev);
+    // the call waits for its copies, which a stream capture cannot hold
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    ce = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+    if (ce) return fail(VX_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(VX_EUNSUPPORTED, "tracing from host memory waits for its copies: not on a capturing stream");
     WaveStaging& W = g_waves[dev];
     std::lock_guard<std::mutex> lock(W.mu);
     int rc = wave_staging(W);

@@ -423,6 +423,33 @@ def test_batch_host_equals_device_batch():
         compare(grids[v], r[idx], full[idx])
 
 
+def test_host_memory_calls_refuse_stream_capture():
+    # the host-memory entry points wait for their copies: on a capturing
+    # stream they refuse before enqueueing anything, and the capture of the
+    # caller's other work stays valid
+    g = synth.terrain_volume(206, 128)
+    vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
+    rays = synth.incoherent_rays(207, 128, 1000)
+    hits = np.empty(len(rays), vx.HIT_DTYPE)
+    vx.trace_batch_host([(vol, rays, hits)])  # uncaptured: works
+    ref = hits.copy()
+    x = torch.zeros(1, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        x.add_(1)
+        with pytest.raises(vx.VxError):
+            vx.trace_batch_host([(vol, rays, hits)])
+        with pytest.raises(vx.VxError):
+            vol.trace_host(rays, out=hits)
+        with pytest.raises(vx.VxError):
+            vol.render_host(synth.camera(208, 128, 64, 48, mode="above"))
+        x.add_(1)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert x.item() == 2
+    assert np.array_equal(hits.view(np.uint8), ref.view(np.uint8))
+
+
 def test_batch_in_cuda_graph():
     vols, grids, sets = _batch_setup(202, 24)
     dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
