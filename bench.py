@@ -728,8 +728,9 @@ def run_headline(args):
 
 
 def sweep_formats(args, vx, torch, sc, g8, peak):
-    """Config 3: every 2048^3 format of Table 2 (and one more): size, Mrays/s
-    of 8 1080p views (vx_render) and of 8 AO rays per primary hit (vx_trace,
+    """Every 2048^3 format of Table 2 (and one more): size, Mrays/s of 8
+    1080p views (vx_render_views: one launch; and one vx_render per view)
+    and of 8 AO rays per primary hit (vx_trace,
     autotuned), algorithmic bytes per ray from the instrumented kernel and the
     achieved fraction of HBM bandwidth; stack vs restarting traversal."""
     import synth
@@ -757,7 +758,9 @@ def sweep_formats(args, vx, torch, sc, g8, peak):
         ao = torch.cat([vx.raygen_ao(r, h, seed=SEED3, spp=8) for r, h in zip(rays, hits)])
         ao_hits = vx.alloc_hits(ao.shape[0])
         tune = v.autotune(ao[: 1 << 20]) if not args.no_tune else None
-        ms_prim = _timed(torch, lambda: [v.render(c, h) for c, h in zip(cams, hits)], args.sweep_steps, 1)
+        # the 8 views in one vx_render_views call (one launch), and one vx_render per view
+        ms_prim = _timed(torch, lambda: v.render_views(cams, hits), args.sweep_steps, 1)
+        ms_prim_each = _timed(torch, lambda: [v.render(c, h) for c, h in zip(cams, hits)], args.sweep_steps, 1)
         ms_ao = _timed(torch, lambda: v.trace(ao, ao_hits), args.sweep_steps, 1)
         n_ao_live = int((ao[:, 7] > 0).sum().item())
         # algorithmic bytes: node words the instrumented kernel reads, plus
@@ -796,6 +799,7 @@ def sweep_formats(args, vx, torch, sc, g8, peak):
                     "bytes_per_voxel": round(st["device_bytes"] / 2048 ** 3, 6),
                     "bytes_per_occupied_voxel": round(st["device_bytes"] / max(1, st["occupied_voxels"]), 4),
                     "mrays_s_primary": round(len(cams) * n_prim / ms_prim / 1e3, 1),
+                    "mrays_s_primary_view_per_launch": round(len(cams) * n_prim / ms_prim_each / 1e3, 1),
                     "mrays_s_ao": round(ao.shape[0] / ms_ao / 1e3, 1),
                     "mrays_s": round((len(cams) * n_prim + ao.shape[0]) / (ms_prim + ms_ao) / 1e3, 1),
                     "ao_rays": int(ao.shape[0]), "ao_rays_live": n_ao_live,
@@ -810,7 +814,7 @@ def sweep_formats(args, vx, torch, sc, g8, peak):
 
 
 def serve_rows(args, vx, torch, sc, g8, rhos, requests, warm):
-    """Config 5: Poisson render requests over 6 resident formats of the 512^3
+    """Serving: Poisson render requests over 6 resident formats of the 512^3
     and 2048^3 volumes; continuous batching vs the serial plain path."""
     import synth
     from paper_2410_14128_b300 import serve
@@ -1222,7 +1226,7 @@ def run_terrain512(args, emit=True):
 # Other workloads (one JSON line each)
 # ---------------------------------------------------------------------------
 def run_sweep(args):
-    """Config 3 alone: the 2048^3 sweep as its own line."""
+    """The 2048^3 Table 2 sweep as its own line."""
     import torch
     import paper_2410_14128_b300 as vx
     sc, g8 = _scene2048()
@@ -1359,7 +1363,7 @@ def run_buildmem(args):
 
 
 def run_serve(args):
-    """Config 5 alone."""
+    """The serving measurement as its own line."""
     import torch
     import paper_2410_14128_b300 as vx
     sc, g8 = _scene2048()

@@ -481,6 +481,16 @@ int vx_raygen_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed
 int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t hit_layout, const vx_trace_opts* opts,
               void* stream);
 
+/* Several camera views of one volume in one call: view k renders cams[k]
+ * into hits[k] (device, per hit_layout, one record per pixel as for
+ * vx_render).  In plain mode (the default) up to 16 views share one launch
+ * (one grid layer per view, the tiles of all views in flight together), so
+ * the views' last warps overlap instead of each view draining the GPU
+ * alone; results are those of one vx_render per view.  VX_MODE_PERSISTENT
+ * renders one view per launch.  Errors as vx_render, naming the view. */
+int vx_render_views(vx_volume v, const vx_camera* cams, uint32_t count, void* const* hits, int32_t hit_layout,
+                    const vx_trace_opts* opts, void* stream);
+
 /* Same as vx_render with the hits copied to host memory; returns when they
  * are there.  VX_EUNSUPPORTED on a stream being captured into a CUDA graph. */
 int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host, int32_t hit_layout,

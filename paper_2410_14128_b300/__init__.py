@@ -118,6 +118,9 @@ _SIGS = {
                                     ctypes.c_void_p]),
     "vx_render": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
                                  ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_render_views": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(_TraceOpts),
+                                       ctypes.c_void_p]),
     "vx_render_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Camera), ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
     "vx_last_error": (ctypes.c_char_p, []),
@@ -413,6 +416,17 @@ class Volume:
         o = _opts(**opts)
         _check(lib().vx_render(self._h, ctypes.byref(c), ctypes.c_void_p(hits.data_ptr()), layout, ctypes.byref(o),
                                _stream_handle(stream)))
+        return hits
+
+    def render_views(self, cams, hits, layout: int = HIT_FULL, stream=None, **opts):
+        """cams: list of camera dicts; hits: list of device hit tensors, one
+        per view (width * height records each); one vx_render_views call."""
+        if len(cams) != len(hits):
+            raise ValueError("one hit tensor per camera")
+        cs = (_Camera * max(1, len(cams)))(*[_camera(c) for c in cams])
+        hp = (ctypes.c_void_p * max(1, len(hits)))(*[h.data_ptr() for h in hits])
+        o = _opts(**opts)
+        _check(lib().vx_render_views(self._h, cs, len(cams), hp, layout, ctypes.byref(o), _stream_handle(stream)))
         return hits
 
     def render_host(self, cam: dict, layout: int = HIT_FULL, out: np.ndarray | None = None, stream=None,

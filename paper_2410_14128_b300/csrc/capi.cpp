@@ -661,6 +661,29 @@ extern "C" int vx_render(vx_volume v, const vx_camera* cam, void* hits, int32_t 
     return launch_render(v->v, cp, 0, n, hits, hit_layout, opts, stream);
 }
 
+extern "C" int vx_render_views(vx_volume v, const vx_camera* cams, uint32_t count, void* const* hits,
+                               int32_t hit_layout, const vx_trace_opts* opts, void* stream) {
+    clear_error();
+    if (count == 0) return VX_OK;
+    if (!cams || !hits) return fail(VX_EINVAL, "cams or hits is NULL");
+    if (count > 65536) return fail(VX_EINVAL, "at most 65536 views per call");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    std::vector<CameraParams> cps(count);
+    std::vector<uint64_t> i0(count, 0), n(count);
+    for (uint32_t k = 0; k < count; k++) {
+        rc = camera_params(&cams[k], &cps[k]);
+        if (rc) return fail(rc, "view %u: %s", k, vx_last_error());
+        n[k] = (uint64_t)cps[k].W * cps[k].H;
+        rc = check_trace_args(v, nullptr, n[k], hits[k], hit_layout);
+        if (!rc) rc = check_ptrs(nullptr, hits[k], hit_layout);
+        if (rc) return fail(rc, "view %u: %s", k, vx_last_error());
+    }
+    DeviceScope ds(v->v.device);
+    if (ds.error()) return cuda_fail(ds.error(), "cudaSetDevice");
+    return launch_render_views(v->v, cps.data(), i0.data(), n.data(), hits, (int)count, hit_layout, opts, stream);
+}
+
 extern "C" int vx_render_host(vx_volume v, const vx_camera* cam, void* hits_host, int32_t hit_layout,
                               const vx_trace_opts* opts, void* stream) {
     clear_error();

@@ -271,22 +271,33 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
 
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream) {
+    return launch_render_views(v, &cp, &i0, &n, &hits, 1, layout, o, stream);
+}
+
+int launch_render_views(const Volume& v, const CameraParams* cps, const uint64_t* i0, const uint64_t* n,
+                        void* const* hits, int count, int layout, const vx_trace_opts* o, void* stream) {
     const int mode = (o && o->mode != VX_MODE_AUTO) ? o->mode : VX_MODE_PLAIN;  // coherent views: plain
     // the tiled render kernel defaults to blocks of 128 (4 tiles of 8 x 4
     // pixels): 2% faster than 256 on the 1080p benchmark views
     const int block = (o && o->block > 0) ? o->block : (mode == VX_MODE_PERSISTENT ? pick_block(o) : 128);
-    int e;
+    int e = 0;
     if (mode == VX_MODE_PERSISTENT) {
-        unsigned long long* next = v.queue_counter(stream);
-        if (!next)
-            return fail(VX_EUNSUPPORTED, "no queue counter for the persistent kernel (at most %d captured "
-                        "persistent launches per volume)", kQueueCaptured);
+        // one persistent launch per view
         const int refill = (o && o->refill > 0) ? o->refill : kDefaultRefill;
         const int burst = (o && o->burst > 0) ? o->burst : kDefaultBurst;
-        e = v.kernels->render_persistent(v.spec.fmt, img_of(v), to_dev(cp), i0, n, hits, layout, block,
-                                         refill, burst, (cudaStream_t)stream, next);
+        for (int k = 0; k < count && !e; k++) {
+            if (n[k] == 0) continue;
+            unsigned long long* next = v.queue_counter(stream);
+            if (!next)
+                return fail(VX_EUNSUPPORTED, "no queue counter for the persistent kernel (at most %d captured "
+                            "persistent launches per volume)", kQueueCaptured);
+            e = v.kernels->render_persistent(v.spec.fmt, img_of(v), to_dev(cps[k]), i0[k], n[k], hits[k], layout,
+                                             block, refill, burst, (cudaStream_t)stream, next);
+        }
     } else {
-        e = v.kernels->render(v.spec.fmt, img_of(v), to_dev(cp), i0, n, hits, layout, block,
+        std::vector<CamDev> cams((size_t)count);
+        for (int k = 0; k < count; k++) cams[(size_t)k] = to_dev(cps[k]);
+        e = v.kernels->render(v.spec.fmt, img_of(v), cams.data(), i0, n, hits, count, layout, block,
                               (cudaStream_t)stream);
     }
     if (e) return fail(VX_ECUDA, "render launch failed: %s", cudaGetErrorString((cudaError_t)e));

@@ -1158,26 +1158,41 @@ __global__ void __launch_bounds__(256, VX_PERSIST_MINB) k_trace_batch(F f, const
     }
 }
 
+// Up to kMaxViews camera views rendered by one launch (blockIdx.z = view):
+// the views' tails overlap instead of each launch draining the GPU alone.
+// View k renders its pixels [i0[k], i0[k] + n[k]) (row-major, hit index
+// pixel - i0[k]) into hits[k]; y0[k] is the row of pixel i0[k].
+constexpr int kMaxViews = 16;
+struct ViewTable {
+    CamDev cam[kMaxViews];
+    void* hits[kMaxViews];
+    uint64_t i0[kMaxViews], n[kMaxViews];
+    uint32_t y0[kMaxViews];
+};
+
 template <class F, int LAYOUT>
-__global__ void VX_PLAIN_BOUNDS k_render(F f, const Img pool, CamDev cam, uint64_t i0,
-                                                uint64_t n, uint32_t y0, void* __restrict__ hits) {
+__global__ void VX_PLAIN_BOUNDS k_render(F f, const Img pool, const __grid_constant__ ViewTable vt, uint32_t yoff) {
     // Each warp takes a tile of 8 x 4 pixels: neighbouring rays follow nearly
     // the same path through the format, and a compact tile has fewer lanes on
     // a silhouette than a 32-pixel run.  blockIdx.y is the tile row (image
-    // rows y0 + 4 blockIdx.y ...), the x threads run along it, a warp per
-    // tile, so no thread divides to find its pixel.  Pixels outside the image
-    // or outside [i0, i0 + n) are skipped.
+    // rows y0 + yoff + 4 blockIdx.y ...), the x threads run along it, a warp
+    // per tile, so no thread divides to find its pixel.  Pixels outside the
+    // view's image or outside its [i0, i0 + n) are skipped (views of
+    // different sizes share one grid).
+    const int vi = (int)blockIdx.z;
+    const CamDev& cam = vt.cam[vi];
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t px = (t >> 5) * kTileW + (lane % kTileW);
-    const uint64_t py = (uint64_t)y0 + (uint64_t)blockIdx.y * kTileH + (lane / kTileW);
+    const uint64_t py = (uint64_t)vt.y0[vi] + yoff + (uint64_t)blockIdx.y * kTileH + (lane / kTileW);
     if (px >= cam.W) return;
     const uint64_t i = py * cam.W + px;
-    if (i < i0 || i - i0 >= n) return;
+    const uint64_t i0 = vt.i0[vi];
+    if (i < i0 || i - i0 >= vt.n[vi]) return;
     const RayIn r = pinhole_ray(cam, px, (uint32_t)py);
     Cnt cnt;
     const HitRec h = trace_ray<false>(f, pool, r, cnt);
-    store_hit<LAYOUT>(f, hits, i - i0, h);
+    store_hit<LAYOUT>(f, vt.hits[vi], i - i0, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -1190,8 +1205,9 @@ struct KernelSet {
     // stack: 0 full node stack, -1 restarting traversal (Sec. 4.4), D in {1, 2, 4, 8}: short stack of depth D
     int (*trace)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n,
                  void* hits, int layout, int block, int stack, cudaStream_t st);
-    int (*render)(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n, void* hits,
-                  int layout, int block, cudaStream_t st);
+    // count views: view k renders pixels [i0[k], i0[k] + n[k]) of cams[k] into hits[k]
+    int (*render)(const FmtParams& p, const Img pool, const CamDev* cams, const uint64_t* i0, const uint64_t* n,
+                  void* const* hits, int count, int layout, int block, cudaStream_t st);
     int (*trace_count)(const FmtParams& p, const Img pool, const float4* rays, uint64_t n, void* hits,
                        int layout, int block, int restart, cudaStream_t st, unsigned long long* counters,
                        uint32_t* sectors);
@@ -1365,29 +1381,50 @@ struct Launch {
                                                                          refill, burst);
         return (int)cudaGetLastError();
     }
-    static int render(const FmtParams& p, const Img pool, const CamDev& cam, uint64_t i0, uint64_t n,
-                      void* hits, int layout, int block, cudaStream_t st) {
-        if (n == 0) return 0;
+    static int render(const FmtParams& p, const Img pool, const CamDev* cams, const uint64_t* i0, const uint64_t* n,
+                      void* const* hits, int count, int layout, int block, cudaStream_t st) {
         const F f = make(p);
-        // 8 x 4 pixel tiles over the image rows that hold pixels i0 .. i0 + n - 1;
-        // one grid row per tile row, at most 65535 tile rows per launch
-        const uint64_t y0 = i0 / cam.W, y1 = (i0 + n - 1) / cam.W;
-        const uint64_t tiles_w = (cam.W + kTileW - 1) / kTileW, tile_rows = (y1 - y0 + kTileH) / kTileH;
-        const uint64_t row_threads = tiles_w * 32u;
-        if (row_threads + (uint64_t)block > 0xFFFFFFFFull) return (int)cudaErrorInvalidConfiguration;
-        const unsigned gx = (unsigned)((row_threads + (uint64_t)block - 1) / (uint64_t)block);
         const size_t sm = stack_bytes(p.J, block);
         prefer_carveout(layout == 0 ? (const void*)k_render<F, 0> : (const void*)k_render<F, 1>, sm, block);
         constexpr uint64_t kMaxRows = 65535;
-        for (uint64_t r = 0; r < tile_rows; r += kMaxRows) {
-            const dim3 grid(gx, (unsigned)(tile_rows - r < kMaxRows ? tile_rows - r : kMaxRows));
-            const uint32_t yr = (uint32_t)(y0 + r * kTileH);
-            if (layout == 0)
-                k_render<F, 0><<<grid, block, sm, st>>>(f, pool, cam, i0, n, yr, hits);
-            else
-                k_render<F, 1><<<grid, block, sm, st>>>(f, pool, cam, i0, n, yr, hits);
+        // launches of up to kMaxViews views; 8 x 4 pixel tiles over the image
+        // rows that hold each view's pixels; one grid row per tile row (the
+        // views' largest count, at most 65535 per launch), one grid column
+        // block per `block` threads of the widest view's tile row
+        for (int v0 = 0; v0 < count; v0 += kMaxViews) {
+            ViewTable vt{};
+            int nv = 0;
+            uint64_t rows = 0, row_threads = 0;
+            for (int k = v0; k < count && k < v0 + kMaxViews; k++) {
+                if (n[k] == 0) continue;
+                const CamDev& cam = cams[k];
+                const uint64_t y0 = i0[k] / cam.W, y1 = (i0[k] + n[k] - 1) / cam.W;
+                const uint64_t tiles_w = (cam.W + kTileW - 1) / kTileW;
+                const uint64_t tile_rows = (y1 - y0 + kTileH) / kTileH;
+                if (tile_rows > rows) rows = tile_rows;
+                if (tiles_w * 32u > row_threads) row_threads = tiles_w * 32u;
+                vt.cam[nv] = cam;
+                vt.hits[nv] = hits[k];
+                vt.i0[nv] = i0[k];
+                vt.n[nv] = n[k];
+                vt.y0[nv] = (uint32_t)y0;
+                nv++;
+            }
+            if (nv == 0) continue;
+            if (row_threads + (uint64_t)block > 0xFFFFFFFFull) return (int)cudaErrorInvalidConfiguration;
+            const unsigned gx = (unsigned)((row_threads + (uint64_t)block - 1) / (uint64_t)block);
+            for (uint64_t r = 0; r < rows; r += kMaxRows) {
+                const dim3 grid(gx, (unsigned)(rows - r < kMaxRows ? rows - r : kMaxRows), (unsigned)nv);
+                const uint32_t yoff = (uint32_t)(r * kTileH);
+                if (layout == 0)
+                    k_render<F, 0><<<grid, block, sm, st>>>(f, pool, vt, yoff);
+                else
+                    k_render<F, 1><<<grid, block, sm, st>>>(f, pool, vt, yoff);
+            }
+            const cudaError_t e = cudaGetLastError();
+            if (e) return (int)e;
         }
-        return (int)cudaGetLastError();
+        return 0;
     }
 };
 

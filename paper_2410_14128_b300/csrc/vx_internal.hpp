@@ -179,6 +179,10 @@ int launch_trace_count(const Volume& v, const vx_ray* rays, uint64_t n, void* hi
                        const vx_trace_opts* o, void* stream, unsigned long long* counters, uint32_t* sectors);
 int launch_render(const Volume& v, const CameraParams& cp, uint64_t i0, uint64_t n, void* hits, int layout,
                   const vx_trace_opts* o, void* stream);
+// count views of one volume; view k renders pixels [i0[k], i0[k] + n[k]) of
+// camera k into hits[k] (plain mode: up to 16 views per launch)
+int launch_render_views(const Volume& v, const CameraParams* cps, const uint64_t* i0, const uint64_t* n,
+                        void* const* hits, int count, int layout, const vx_trace_opts* o, void* stream);
 int launch_raygen(const CameraParams& cp, vx_ray* rays, void* stream);
 int launch_ao(const vx_ray* rays, const void* hits, uint64_t n, uint64_t seed, int spp, float eps, float tmax,
               vx_ray* out, void* stream);

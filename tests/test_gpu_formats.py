@@ -16,7 +16,7 @@ size, and checks:
     the canonical (unaligned, unpacked) device image return bit-identical hit
     records on all rays;
   - that the pinhole render kernel returns the same records as a trace of the
-    same camera's rays.
+    same camera's rays, also with two views in one launch.
 
 Workloads: 64^3 value noise (256 x 256 view + incoherent rays); 512^3 terrain
 (1920 x 1080 view + 2^21 incoherent rays); 2048^3 primitive scene (8 views of
@@ -121,6 +121,13 @@ def _check_render(spec, vol, cam):
     vol.render(cam, h)
     ref = _trace(vol, vx.raygen_pinhole(cam), mode=vx.MODE_PLAIN)
     assert torch.equal(h, ref), f"{spec}: render differs from a trace of the camera's rays"
+    # two views in one launch (the second a quarter-size crop of the same camera)
+    small = dict(cam, width=max(1, cam["width"] // 2), height=max(1, cam["height"] // 2))
+    hv = [vx.alloc_hits(cam["width"] * cam["height"]), vx.alloc_hits(small["width"] * small["height"])]
+    vol.render_views([cam, small], hv)
+    hs = vx.alloc_hits(small["width"] * small["height"])
+    vol.render(small, hs)
+    assert torch.equal(hv[0], h) and torch.equal(hv[1], hs), f"{spec}: multi-view render differs"
 
 
 def _sample(n, seed):

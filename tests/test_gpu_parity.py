@@ -252,6 +252,38 @@ def test_render_ragged_tiles_and_chunks(W, H):
     assert np.array_equal(vol.render_host(cam, mode=vx.MODE_PERSISTENT), vx.hits_to_numpy(h1))
 
 
+def test_render_views_equal_single_renders():
+    # vx_render_views: views of different sizes (ragged tiles, one taller
+    # than the others, one wider) share launches of up to 16 views; 20 views
+    # take two launches; both layouts, both modes, and several block sizes
+    g = synth.terrain_volume(45, 128)
+    vol = vx.Volume("R(3,3,3) S(2) G(2)", g)
+    sizes = [(7, 5), (1001, 767), (33, 4097), (320, 180), (64, 64)] * 4
+    cams = [synth.camera(46 + k, 128, w, h, mode="above") for k, (w, h) in enumerate(sizes)]
+    for layout in (vx.HIT_FULL, vx.HIT_COMPACT):
+        ref = []
+        for c in cams:
+            h = vx.alloc_hits(c["width"] * c["height"], layout)
+            vol.render(c, h, layout=layout)
+            ref.append(h)
+        for opts in (dict(), dict(block=64), dict(block=256), dict(mode=vx.MODE_PERSISTENT)):
+            got = [vx.alloc_hits(c["width"] * c["height"], layout) for c in cams]
+            for h in got:
+                h.fill_(-0x55555556)  # a pixel the kernel skipped keeps this pattern
+            vol.render_views(cams, got, layout=layout, **opts)
+            torch.cuda.synchronize()
+            for k, (a, b) in enumerate(zip(ref, got)):
+                assert torch.equal(a, b), (layout, opts, k)
+    # and the traversal against the oracle on one view's own rays
+    c = cams[3]
+    h = vx.alloc_hits(c["width"] * c["height"])
+    vol.render_views([c], [h])
+    t = vx.alloc_hits(c["width"] * c["height"])
+    vol.trace(vx.raygen_pinhole(c), t, mode=vx.MODE_PLAIN)
+    torch.cuda.synchronize()
+    assert torch.equal(h, t)
+
+
 def test_trace_host_multi_chunk():
     g = synth.random_grid(51, (64, 64, 64), 0.03)
     vol = vx.Volume("R(2,2,2) G(4)", g)
