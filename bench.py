@@ -1081,7 +1081,11 @@ def run_terrain512(args, emit=True):
         kname = "k_trace_persistent" if persistent else "k_trace"
         g_sort = tuned[k]["sort_cell_log2"] if tuned else fixed.get("sort", 0)
         if g_sort:
-            kname += f"+sort{g_sort}"  # rays read through the sort's permutation
+            # the sort key keeps at most 5 bits of the origin cell per axis, so
+            # every g below log2(grid) - 5 gives the same key, permutation and
+            # trace as g = log2(grid) - 5: name the counters by that g
+            g_eff = max(g_sort, (N_VOL.bit_length() - 1) - 5)
+            kname += f"+sort{g_eff}"  # the trace of the sorted copy of the rays
     # counters of the same kernel on the same format (a capture of another
     # kernel does not count)
     kernel_key = f"{name}:{FORMATS[k].replace(' ', '')}:{kname}"
