@@ -448,11 +448,14 @@ def run_headline(args):
     total = sum(r.shape[0] for r in rays)
 
     # --- autotune each format on a sample of its own sets (outside timing) ---
-    tuned = []
+    tuned, tuned_batch = [], []
     if not args.no_tune:
         for i, v in enumerate(vols):
             own = torch.cat([rays[k][: 1 << 17] for k in range(i, N_SETS, len(vols))])
             tuned.append(v.autotune(own))
+        # the batched kernel's options per format, timed on its own 16 sets
+        chosen = vx.autotune_batch(sets)
+        tuned_batch = [chosen[i] for i in range(len(vols))]
 
     # --- algorithmic bytes per ray and footprint (instrumented kernel, outside timing) ---
     node_bytes, iters = [], []
@@ -704,7 +707,7 @@ def run_headline(args):
                              f"of hits per step (L2 126 MB)",
                        "hit_layout": "full 16 B", "graph": "one CUDA graph per timed step (vx_trace_batch_timed)",
                        "occupancy": round(sc.occupied / 2048 ** 3, 5),
-                       "tuned_trace_opts": tuned or None},
+                       "tuned_trace_opts": tuned or None, "tuned_batch_opts": tuned_batch or None},
             "batched": {"mrays_s": round(value, 2), "step_ms_median": round(float(np.median(step_ms)), 4),
                         "results_identical_to_plain": ok_same, "groups": n_groups},
             "plain_mrays_s": round(total / ms_plain / 1e3, 2),

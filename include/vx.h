@@ -347,10 +347,10 @@ int vx_trace_counted(vx_volume v, const vx_ray* rays, uint64_t n, void* hits, in
  * nothing and does not synchronise, so it can be captured into a CUDA graph
  * (make one uncaptured call per device first: it creates the library's
  * fork streams).  opts: refill/burst/block as for vx_trace for every group
- * (NULL or VX_MODE_AUTO: the block, refill and burst of the best
- * persistent-kernel options vx_autotune timed for each group's volume, also
- * when it chose the plain kernel for vx_trace; else the defaults); sorting
- * is not supported
+ * (NULL or VX_MODE_AUTO: the options vx_autotune_batch chose for each
+ * group's volume, else block 256, refill 4, burst 16 for every group; the
+ * options vx_autotune picks for vx_trace are not used here); sorting is not
+ * supported
  * here (VX_EUNSUPPORTED).  Calls for one device are enqueued one at a time.
  * (Not in the paper: it traces one frame of one format at a time.) */
 typedef struct vx_batch_item {
@@ -382,7 +382,7 @@ int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit
  * of at most 2^21 rays, taken in item order (an item larger than the room
  * left in a wave is split across waves); each wave is uploaded, traced by
  * the batched kernels (as vx_trace_batch: one persistent kernel per format,
- * each volume's tuned options unless opts is given) and its hits copied
+ * each volume's batched options unless opts is given) and its hits copied
  * back, with four waves in flight on four internal streams, so uploads,
  * kernels and downloads overlap.  The first wave starts after the caller's
  * earlier work on `stream`; the call returns when every hit is in host
@@ -395,14 +395,33 @@ int vx_trace_batch_timed(const vx_batch_item* items, uint32_t count, int32_t hit
 int vx_trace_batch_host(const vx_batch_item* items, uint32_t count, int32_t hit_layout, const vx_trace_opts* opts,
                         void* stream);
 
+/* Picks the batched kernel's options for each volume among the items.  The
+ * objective is the whole call (the groups' kernels run concurrently and
+ * share the SMs): coordinate descent over the refill threshold (1-16),
+ * iterations per refill check (4-32) and block size (128, 256), first for
+ * all volumes together (two rounds), then for each volume with the others
+ * fixed (one round), each candidate timed as the vx_trace_batch call over
+ * all items on `stream` (best of three after one warm-up call; a candidate
+ * replaces the current options only when more than 1% faster), starting
+ * from the options a batched call would use now.  Later vx_trace_batch,
+ * vx_trace_batch_timed and vx_trace_batch_host calls with opts NULL or
+ * VX_MODE_AUTO use them for each volume's group.  Traces every item many
+ * times (hits are overwritten with the same records); synchronises
+ * `stream`.  chosen (optional, count entries) receives, per item, its
+ * volume's options (zeros for a volume with no rays in the items).  Errors
+ * as vx_trace_batch.  (Not in the paper.) */
+int vx_autotune_batch(const vx_batch_item* items, uint32_t count, int32_t hit_layout, void* stream,
+                      vx_trace_opts* chosen);
+
 /* Picks vx_trace options for this volume: times candidates on `rays` (a
  * device sample of the rays the caller will trace, n of them) with CUDA
  * events on `stream` (each candidate the best of three launches) --
- * restarting vs stack traversal, top level in shared memory, coherence-sort
- * granularity, persistent refill threshold, iterations per refill check,
- * block size (two rounds), then the plain kernel at each block size -- by
- * coordinate descent, and
- * keeps the fastest; later vx_trace calls with
+ * restarting vs stack traversal, short-stack depth, shared-memory staging
+ * depth, coherence-sort granularity, persistent refill threshold,
+ * iterations per refill check, block size (two rounds), then the plain
+ * kernel at each block size -- by coordinate descent (a candidate replaces
+ * the current options only when more than 1% faster), and keeps the
+ * result; later vx_trace calls with
  * opts NULL or mode VX_MODE_AUTO use it.  Synchronises `stream`; allocates a
  * temporary n-hit buffer.  best (optional) receives the options, best_ms the
  * sample's time with them.  (Not in the paper: its formats are traced with

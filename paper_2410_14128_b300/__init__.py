@@ -106,6 +106,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_uint32)]),
     "vx_trace_batch_host": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
                                            ctypes.POINTER(_TraceOpts), ctypes.c_void_p]),
+    "vx_autotune_batch": (ctypes.c_int, [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.POINTER(_TraceOpts)]),
     "vx_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                    ctypes.POINTER(_TraceOpts), ctypes.POINTER(ctypes.c_double)]),
     "vx_trace_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
@@ -465,6 +467,21 @@ def trace_batch(items, layout: int = HIT_FULL, stream=None, events=None, **opts)
     _check(lib().vx_trace_batch_timed(arr, len(items), layout, op, _stream_handle(stream), ev, len(events),
                                       ctypes.byref(groups)))
     return groups.value
+
+
+def autotune_batch(items, layout: int = HIT_FULL, stream=None) -> list:
+    """items as for trace_batch (device tensors); one vx_autotune_batch call.
+    Returns, per item, the options its volume's batched group now uses (as
+    a dict)."""
+    arr = (_BatchItem * max(1, len(items)))()
+    for k, (vol, rays, hits) in enumerate(items):
+        arr[k].volume = vol.handle
+        arr[k].rays = rays.data_ptr()
+        arr[k].n = rays.shape[0]
+        arr[k].hits = hits.data_ptr()
+    out = (_TraceOpts * max(1, len(items)))()
+    _check(lib().vx_autotune_batch(arr, len(items), layout, _stream_handle(stream), out))
+    return [_opts_dict(out[k]) for k in range(len(items))]
 
 
 def trace_batch_host(items, layout: int = HIT_FULL, stream=None, **opts) -> None:

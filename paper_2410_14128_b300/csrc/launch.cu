@@ -363,9 +363,10 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
     }
     if (subs.empty()) return VX_OK;
     // Options of each group: explicit ones, else the block, refill and burst
-    // of its volume's best persistent-kernel tuning (the tuned options when
-    // the autotuner chose the persistent kernel, else the best persistent
-    // candidate it timed), else the defaults.
+    // vx_autotune_batch chose for its volume, else the batched defaults.
+    // (A volume's vx_autotune options are tuned on one launch alone and did
+    // not carry over: 2005-2085 Mrays/s over runs against 2075 for the
+    // defaults.)
     const int nsub = (int)subs.size();
     std::vector<vx_trace_opts> gopts(nsub);
     for (int i = 0; i < nsub; i++) {
@@ -373,13 +374,13 @@ int launch_batch(const std::vector<BatchItemIn>& items, int layout, const vx_tra
         if (!o || o->mode == VX_MODE_AUTO) {
             Volume& mv = const_cast<Volume&>(*subs[i].v0);
             std::lock_guard<std::mutex> lock(mv.tune_mu);
-            if (mv.tuned) def = mv.tuned_opts.mode == VX_MODE_PERSISTENT ? mv.tuned_opts : mv.tuned_persistent;
+            if (mv.batch_tuned) def = mv.tuned_batch;
         } else {
             def = *o;
         }
         if (def.block <= 0) def.block = 256;
-        if (def.refill <= 0) def.refill = kDefaultRefill;
-        if (def.burst <= 0) def.burst = kDefaultBurst;
+        if (def.refill <= 0) def.refill = kBatchRefill;
+        if (def.burst <= 0) def.burst = kBatchBurst;
         gopts[i] = def;
     }
 

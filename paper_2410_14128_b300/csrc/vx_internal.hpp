@@ -129,6 +129,12 @@ struct Staging {
 
 constexpr int kDefaultRefill = 8;  // persistent kernel: idle lanes before a warp refills
 constexpr int kDefaultBurst = 4;   // persistent kernel: iterations between refill checks
+// Batched calls without vx_autotune_batch: the same options for every group.
+// Over a grid of block {128, 256} x refill {2..16} x burst {8, 16, 32} on the
+// 2048^3 batched workload, blocks of 256 with refill 4 and burst 16 were
+// fastest (2075 Mrays/s; refill 8 / burst 4: 1987).
+constexpr int kBatchRefill = 4;
+constexpr int kBatchBurst = 16;
 constexpr int kQueueRing = 256;      // queue counters per volume for launches issued directly
 constexpr int kQueueCaptured = 3840;  // further counters, each given to one captured launch for good
 
@@ -149,7 +155,8 @@ struct Volume {
     std::mutex tune_mu;
     bool tuned = false;
     vx_trace_opts tuned_opts{};             // chosen by vx_autotune, used for VX_MODE_AUTO
-    vx_trace_opts tuned_persistent{};       // vx_autotune's best persistent-kernel options (batched groups)
+    bool batch_tuned = false;
+    vx_trace_opts tuned_batch{};            // chosen by vx_autotune_batch for this volume's batched group
     unsigned long long* d_queue = nullptr;  // kQueueRing + kQueueCaptured counters
     mutable std::atomic<uint32_t> queue_slot{0};
     mutable std::atomic<uint32_t> captured_slot{0};

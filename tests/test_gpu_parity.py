@@ -482,6 +482,33 @@ def test_host_memory_calls_refuse_stream_capture():
     assert np.array_equal(hits.view(np.uint8), ref.view(np.uint8))
 
 
+def test_autotune_batch_picks_options_and_keeps_results():
+    # vx_autotune_batch: per volume, options from its grid; batched calls
+    # afterwards use them and still write the plain kernel's hits
+    vols, grids, sets = _batch_setup(209, 24)
+    dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
+    items = [(vols[v], r, h) for v, r, h in dev]
+    chosen = vx.autotune_batch(items)
+    assert len(chosen) == len(items)
+    traced = {v for v, r_np in sets if len(r_np)}
+    for (v, r_np), c in zip(sets, chosen):
+        if v not in traced:  # a volume with no rays in the batch is not tuned
+            continue
+        assert c["mode"] == "persistent" and c["block"] in (64, 128, 256), c
+        assert c["refill"] in (1, 2, 4, 8, 16) and c["burst"] in (4, 8, 16, 32), c
+    for k in range(len(items)):  # one volume, one choice
+        for j in range(len(items)):
+            if sets[k][0] == sets[j][0]:
+                assert chosen[k] == chosen[j]
+    for _, _, h in dev:
+        h.fill_(-1)
+    vx.trace_batch(items)
+    torch.cuda.synchronize()
+    for (v, r_np), (_, r, h) in zip(sets, dev):
+        if len(r_np):
+            assert np.array_equal(vx.hits_to_numpy(h), gpu_trace(vols[v], r_np, mode=vx.MODE_PLAIN))
+
+
 def test_batch_in_cuda_graph():
     vols, grids, sets = _batch_setup(202, 24)
     dev = [(v, torch.from_numpy(r).cuda().reshape(-1, 8), vx.alloc_hits(len(r))) for v, r in sets]
